@@ -1,0 +1,428 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+Each test checks the oracle against something other than its own formulas:
+published known-answer vectors, closed forms, invariants, special cases that
+reduce to a textbook result, quadrature of small Boltzmann distributions,
+or brute-force limits.  None of them needs a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+import oracle
+
+TWO_PI = 2.0 * math.pi
+
+
+def _batch_mean_err(x, nb=40):
+    """Mean and batch-means standard error of an autocorrelated series."""
+    x = np.asarray(x, dtype=np.float64)
+    m = len(x) // nb
+    b = x[: m * nb].reshape(nb, m).mean(axis=1)
+    return x.mean(), b.std(ddof=1) / math.sqrt(nb)
+
+
+# ----------------------------------------------------------------- Philox
+
+def test_philox_known_answers(golden_dir):
+    """Philox4x32-10 reproduces the generator's published known-answer vectors."""
+    n = 0
+    with open(os.path.join(golden_dir, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(t, 16) for t in line.split()]
+            out = oracle.philox4x32_10(w[0:4], w[4:6])
+            assert list(out) == w[6:10]
+            n += 1
+    assert n == 3
+
+
+def test_hot_start_uniform_range():
+    """Hot start draws gap angles in [0, 2 pi) and leaves sample sites alone (Alg. 2 step 1.8)."""
+    L = 64
+    gap = np.zeros((L, L), np.uint8)
+    gap[::2, :] = 1
+    phi = np.full((L, L), 1.25)
+    out = oracle.hot_start(phi, gap, seed=7, img=0, chain=3)
+    g = out[gap == 1]
+    assert np.all(g >= 0) and np.all(g < TWO_PI)
+    assert np.all(out[gap == 0] == 1.25)
+    # the uniforms are 24-bit: 2 pi * k / 2^24 exactly representable multiples
+    k = g / TWO_PI * 2**24
+    assert np.allclose(k, np.round(k), atol=1e-6)
+    # roughly uniform: mean and variance of U(0, 2 pi)
+    assert abs(g.mean() - math.pi) < 0.1
+    assert abs(g.var() - TWO_PI**2 / 12) < 0.3
+    other = oracle.hot_start(phi, gap, seed=7, img=0, chain=4)
+    assert not np.array_equal(out, other)
+
+
+# ------------------------------------------------------------ map, Eq. map
+
+def test_map_round_trip_and_range():
+    rng = np.random.default_rng(0)
+    z = rng.normal(50, 10, (17, 23))
+    gap = (rng.random(z.shape) < 0.4).astype(np.uint8)
+    phi, zmin, zmax = oracle.map_to_angles(z, gap)
+    s = gap == 0
+    assert zmin == z[s].min() and zmax == z[s].max()
+    assert phi[s].min() == 0.0
+    assert abs(phi[s].max() - TWO_PI) < 1e-15
+    assert np.all(phi[s] >= 0) and np.all(phi[s] <= TWO_PI)
+    back = oracle.unmap(phi[s], zmin, zmax)
+    assert np.max(np.abs(back - z[s])) < 1e-12
+    # monotone: order of values preserved
+    order = np.argsort(z[s])
+    assert np.all(np.diff(phi[s][order]) >= 0)
+
+
+def test_map_hand_example():
+    z = np.array([[10.0, 20.0], [30.0, 50.0]])
+    gap = np.array([[0, 0], [0, 1]], np.uint8)  # 50 is missing: range is [10, 30]
+    phi, zmin, zmax = oracle.map_to_angles(z, gap)
+    assert (zmin, zmax) == (10.0, 30.0)
+    assert np.allclose(phi, [[0.0, math.pi], [TWO_PI, 0.0]])
+
+
+def test_map_degenerate_range():
+    z = np.full((3, 3), 2.0)
+    gap = np.zeros((3, 3), np.uint8)
+    with pytest.raises(ValueError):
+        oracle.map_to_angles(z, gap)
+
+
+# ------------------------------------------------------- energies, Eq. 3/4/6
+
+def test_bond_count_matches_paper():
+    """N_GP = 2 L (L - 1) on an L x L grid with open boundaries (Eq. ene)."""
+    for L in (2, 3, 16, 101):
+        assert oracle.n_bonds(L, L) == 2 * L * (L - 1)
+    assert oracle.n_bonds(5, 1) == 4
+
+
+def test_energy_closed_forms():
+    L = 9
+    J = 1.7
+    # aligned ground state: every bond cos(0) = 1
+    assert oracle.energy(np.full((L, L), 2.0), J=J) == pytest.approx(-J * 2 * L * (L - 1))
+    # checkerboard of 0 and 2 pi: every bond cos(q 2 pi) = cos(pi) = -1 (the maximum for q = 1/2)
+    cb = np.fromfunction(lambda y, x: ((x + y) % 2) * TWO_PI, (L, L))
+    assert oracle.energy(cb, J=J) == pytest.approx(J * 2 * L * (L - 1))
+    # horizontal ramp of slope c: horizontal bonds cos(q c), vertical bonds 1
+    c = 0.3
+    ramp = np.fromfunction(lambda y, x: c * x, (L, L))
+    nh, nv = L * (L - 1), L * (L - 1)
+    assert oracle.energy(ramp, q=0.5) == pytest.approx(-(nh * math.cos(0.5 * c) + nv))
+    # shift invariance (energy depends on contrasts only)
+    rng = np.random.default_rng(1)
+    p = rng.uniform(0, 3, (L, L))
+    assert oracle.energy(p + 1.0) == pytest.approx(oracle.energy(p), rel=1e-13)
+
+
+def test_energy_monotone_in_contrast():
+    """For q <= 1/2 the pair energy -cos(q d) increases monotonically on d in [0, 2 pi] (Sec. 2.2)."""
+    d = np.linspace(0, TWO_PI, 200)
+    e = [oracle.energy(np.array([[0.0, di]])) for di in d]
+    assert np.all(np.diff(e) > 0)
+    # and for q = 1 it does not (degenerate contrasts d and 2 pi - d)
+    e1 = [oracle.energy(np.array([[0.0, di]]), q=1.0) for di in (1.0, TWO_PI - 1.0)]
+    assert e1[0] == pytest.approx(e1[1])
+
+
+def test_sample_energy_closed_forms():
+    L = 8
+    gap = np.zeros((L, L), np.uint8)
+    gap[3, 3] = 1
+    # aligned samples -> e_s = -J
+    e, n = oracle.sample_energy(np.full((L, L), 1.0), gap, J=1.0)
+    assert e == pytest.approx(-1.0) and n == 2 * L * (L - 1) - 4
+    # only horizontal pairs, slope c: e_s = -cos(q c)
+    c = 0.8
+    ramp = np.fromfunction(lambda y, x: c * x, (1, L))
+    e, n = oracle.sample_energy(ramp, np.zeros((1, L), np.uint8))
+    assert n == L - 1 and e == pytest.approx(-math.cos(0.5 * c))
+    # isolated samples (no sample pairs) -> N_SP = 0
+    cb_gap = np.fromfunction(lambda y, x: (x + y) % 2, (L, L)).astype(np.uint8)
+    e, n = oracle.sample_energy(np.zeros((L, L)), cb_gap)
+    assert n == 0 and math.isnan(e)
+
+
+def test_torque_matches_finite_differences():
+    """dH/dphi by central differences (h = 1e-3, FP64) and dH/dJ = H / J."""
+    rng = np.random.default_rng(2)
+    p = rng.uniform(0, TWO_PI, (6, 7))
+    J = 1.3
+    g = oracle.torque(p, q=0.5, J=J)
+    h = 1e-3
+    fd = np.zeros_like(p)
+    for i in range(p.shape[0]):
+        for j in range(p.shape[1]):
+            a = p.copy(); a[i, j] += h
+            b = p.copy(); b[i, j] -= h
+            fd[i, j] = (oracle.energy(a, J=J) - oracle.energy(b, J=J)) / (2 * h)
+    assert np.max(np.abs(g - fd)) < 1e-6
+    dJ = (oracle.energy(p, J=J + h) - oracle.energy(p, J=J - h)) / (2 * h)
+    assert dJ == pytest.approx(oracle.energy(p, J=J) / J, rel=1e-9)
+
+
+# ---------------------------------------------------- over-relaxation, Eq. 8
+
+def _site_energy(v, nbr, q):
+    return -sum(math.cos(q * (v - t)) for t in nbr)
+
+
+def test_over_relaxation_conserves_site_energy():
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    moved = 0
+    for _ in range(20000):
+        n = int(rng.integers(1, 5))
+        nbr = rng.uniform(0, TWO_PI, n)
+        phi = rng.uniform(0, TWO_PI)
+        p1, _, _ = oracle.over_relax(phi, nbr, q=0.5)
+        assert 0.0 <= p1 < TWO_PI
+        worst = max(worst, abs(_site_energy(p1, nbr, 0.5) - _site_energy(phi, nbr, 0.5)))
+        moved += p1 != phi
+    assert worst < 1e-12
+    assert moved > 10000  # most cases do reflect
+
+
+def test_over_relaxation_is_an_involution():
+    rng = np.random.default_rng(4)
+    for _ in range(5000):
+        nbr = rng.uniform(0, TWO_PI, int(rng.integers(2, 5)))
+        phi = rng.uniform(0, TWO_PI)
+        p1, _, _ = oracle.over_relax(phi, nbr)
+        p2, _, _ = oracle.over_relax(p1, nbr)
+        assert abs(p2 - phi) < 1e-11
+
+
+def test_over_relaxation_q1_is_the_printed_formula():
+    """For q = 1 the reflection reduces to phi' = (2 Phi - phi) mod 2 pi of Eq. over-relax."""
+    rng = np.random.default_rng(5)
+    for _ in range(2000):
+        nbr = rng.uniform(0, TWO_PI, int(rng.integers(1, 5)))
+        phi = rng.uniform(0, TWO_PI)
+        printed = (2 * math.atan2(np.sin(nbr).sum(), np.cos(nbr).sum()) - phi) % TWO_PI
+        a, _, _ = oracle.over_relax(phi, nbr, q=1.0)
+        b, _, _ = oracle.over_relax(phi, nbr, q=0.5, literal=True)
+        assert abs(a - printed) < 1e-12 and abs(b - printed) < 1e-12
+
+
+def test_printed_q1_formula_does_not_conserve_q_half_energy():
+    """The printed (q = 1) reflection breaks energy conservation for q = 1/2."""
+    rng = np.random.default_rng(6)
+    d = []
+    for _ in range(2000):
+        nbr = rng.uniform(0, TWO_PI, 4)
+        phi = rng.uniform(0, TWO_PI)
+        p1, _, _ = oracle.over_relax(phi, nbr, q=0.5, literal=True)
+        d.append(abs(_site_energy(p1, nbr, 0.5) - _site_energy(phi, nbr, 0.5)))
+    assert np.mean(d) > 0.3
+
+
+def test_over_relaxation_zero_field():
+    """atan2 needs |x| + |y| > 0: with a vanishing field the spin is left alone."""
+    p1, _, field = oracle.over_relax(1.0, np.array([0.0, TWO_PI]), q=0.5)
+    assert field < 1e-12 and p1 == 1.0
+
+
+# -------------------------------------------------- Metropolis limits, Alg. 1
+
+def _gappy(L, frac, seed):
+    rng = np.random.default_rng(seed)
+    gap = (rng.random((L, L)) < frac).astype(np.uint8)
+    phi = np.where(gap == 1, 0.0, rng.uniform(0, TWO_PI, (L, L)))
+    return oracle.hot_start(phi, gap, seed=seed, img=0, chain=0), gap
+
+
+def test_zero_temperature_never_raises_energy():
+    phi, gap = _gappy(16, 0.5, 8)
+    H = oracle.energy(phi)
+    for s in range(40):
+        phi, _ = oracle.sweep(phi, gap, T=1e-300, a=2.0, seed=9, sweep_index=s)
+        H1 = oracle.energy(phi)
+        assert H1 <= H + 1e-11
+        H = H1
+
+
+def test_infinite_temperature_accepts_everything():
+    phi, gap = _gappy(12, 0.6, 10)
+    P = int(gap.sum())
+    for s in range(5):
+        phi, n_acc = oracle.sweep(phi, gap, T=1e300, a=1.0, seed=11, sweep_index=s)
+        assert n_acc == P
+
+
+def test_sample_sites_are_never_touched():
+    phi, gap = _gappy(10, 0.3, 12)
+    out, _ = oracle.sweep(phi, gap, T=0.3, a=1.5, seed=13)
+    assert np.array_equal(out[gap == 0], phi[gap == 0])
+    assert np.all(out[gap == 1] >= 0) and np.all(out[gap == 1] < TWO_PI)
+
+
+def test_adaptation_rule():
+    """Alg. 2 step 4.2: a(i+1) = 1 + (i+1)/k_a when A < A_targ, else a is kept."""
+    assert oracle.adapt_a(1.0, 29, 100, 5) == pytest.approx(1 + 6 / 3)
+    assert oracle.adapt_a(1.7, 30, 100, 5) == 1.7
+    assert oracle.adapt_a(1.0, 0, 10, 0, A_targ=0.3, k_a=3) == pytest.approx(4 / 3)
+
+
+# --------------------------------------------- equilibrium pins, Sec. 2.2-2.3
+
+def test_high_temperature_limit():
+    """At beta = 0 angles are i.i.d. U(0, 2 pi): <cos(dphi / 2)> = 4 / pi^2, so e -> -4/pi^2."""
+    m, _ = oracle.e_of_T(1e8, L=16, K=4, n_eq=20, n_meas=300, seed=14)
+    # standard error per bond ~ sqrt(0.34 / (480 * 1200)) ~ 8e-4
+    assert abs(m + 4 / math.pi**2) < 4e-3
+
+
+def test_low_temperature_slope():
+    """Harmonic limit (derived, loose): e ~ -1 + T/4 for large L as T -> 0."""
+    m, _ = oracle.e_of_T(0.01, L=32, K=2, n_eq=150, n_meas=100, seed=15)
+    assert abs((m + 1.0) - 0.0025) < 0.1 * 0.0025
+
+
+def test_q1_open_chain_matches_bessel_ratio():
+    """q = 1 open chain: e = -I1(beta) / I0(beta) (Sec. 5.1, eq. ene_1D)."""
+    T = 0.5
+    beta = 1.0 / T
+    # run the chain directly: a 1 x 64 lattice with every site free
+    L = 64
+    gap = np.ones((1, L), np.uint8)
+    phi = oracle.hot_start(np.zeros((1, L)), gap, seed=16, img=0, chain=0)
+    es = []
+    for s in range(6000):
+        phi, _ = oracle.sweep(phi, gap, T=T, a=1.0, seed=16, sweep_index=s, q=1.0)
+        if s >= 200:
+            es.append(oracle.energy(phi, q=1.0) / (L - 1))
+    mean, err = _batch_mean_err(es)
+    exact = -special.i1(beta) / special.i0(beta)
+    assert abs(mean - exact) < 4 * err + 1e-4, (mean, exact, err)
+
+
+def test_q_half_chain_differs_from_bessel_ratio():
+    """On the segment (q = 1/2) the Bessel closed form does not hold (checked by transfer operator)."""
+    T = 0.5
+    beta = 1.0 / T
+    x, w = np.polynomial.legendre.leggauss(200)
+    t = np.pi * (x + 1.0)
+    w = np.pi * w
+    K = np.exp(beta * np.cos(0.5 * (t[:, None] - t[None, :])))
+    Kc = np.cos(0.5 * (t[:, None] - t[None, :])) * K
+    # open chain of 2 sites: one bond, <cos> = int int cos K / int int K
+    exact_seg = -(w @ Kc @ w) / (w @ K @ w)
+    bessel = -special.i1(beta) / special.i0(beta)
+    assert abs(exact_seg - bessel) > 0.05
+    gap = np.ones((1, 2), np.uint8)
+    phi = oracle.hot_start(np.zeros((1, 2)), gap, seed=17, img=0, chain=0)
+    es = []
+    for s in range(30000):
+        phi, _ = oracle.sweep(phi, gap, T=T, a=1.0, seed=17, sweep_index=s)
+        if s >= 100:
+            es.append(oracle.energy(phi))
+    mean, err = _batch_mean_err(es)
+    assert abs(mean - exact_seg) < 4 * err + 2e-3, (mean, exact_seg, err)
+
+
+def _mc_series(phi, gap, T, a, n, seed, burn=200, q=0.5, fn=None):
+    out = []
+    for s in range(n + burn):
+        phi, _ = oracle.sweep(phi, gap, T=T, a=a, seed=seed, sweep_index=s, q=q)
+        if s >= burn:
+            out.append(fn(phi))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("a", [1.0, 3.0])
+def test_three_site_chain_marginal_by_quadrature(a):
+    """Middle spin of a 3-site chain with both ends sampled: Boltzmann conditional by 1-D quadrature."""
+    T = 0.4
+    ea, eb = 1.0, 4.0
+    dens = lambda v: math.exp((math.cos(0.5 * (v - ea)) + math.cos(0.5 * (v - eb))) / T)
+    Z = integrate.quad(dens, 0, TWO_PI, limit=200)[0]
+    m1 = integrate.quad(lambda v: v * dens(v), 0, TWO_PI, limit=200)[0] / Z
+    cdf_pts = [1.5, 2.5, 3.5]
+    cdf = [integrate.quad(dens, 0, c, limit=200)[0] / Z for c in cdf_pts]
+    gap = np.array([[0, 1, 0]], np.uint8)
+    phi = np.array([[ea, 0.0, eb]])
+    phi = oracle.hot_start(phi, gap, seed=18, img=0, chain=0)
+    xs = _mc_series(phi, gap, T, a, 40000, seed=19, fn=lambda p: p[0, 1])
+    mean, err = _batch_mean_err(xs)
+    assert abs(mean - m1) < 4 * err + 1e-3, (mean, m1, err)
+    for c, F in zip(cdf_pts, cdf):
+        ind = (xs < c).astype(float)
+        fm, fe = _batch_mean_err(ind)
+        assert abs(fm - F) < 4 * fe + 2e-3, (c, fm, F, fe)
+
+
+def test_two_by_two_conditional_by_quadrature():
+    """2 x 2 lattice, top row sampled, bottom row free: joint of two spins by 2-D quadrature."""
+    T = 0.3
+    sa, sb = 2.0, 5.0
+    x, w = np.polynomial.legendre.leggauss(160)
+    t = np.pi * (x + 1.0)
+    w = np.pi * w
+    U, V = np.meshgrid(t, t, indexing="ij")
+    W = w[:, None] * w[None, :]
+    dens = np.exp((np.cos(0.5 * (U - sa)) + np.cos(0.5 * (V - sb)) + np.cos(0.5 * (U - V))) / T) * W
+    Z = dens.sum()
+    mu = (U * dens).sum() / Z
+    mv = (V * dens).sum() / Z
+    mc = (np.cos(0.5 * (U - V)) * dens).sum() / Z
+    gap = np.array([[0, 0], [1, 1]], np.uint8)
+    phi = oracle.hot_start(np.array([[sa, sb], [0.0, 0.0]]), gap, seed=20, img=0, chain=0)
+    xs = _mc_series(phi, gap, T, 2.0, 40000, seed=21,
+                    fn=lambda p: (p[1, 0], p[1, 1], math.cos(0.5 * (p[1, 0] - p[1, 1]))))
+    for k, exact in enumerate((mu, mv, mc)):
+        m, e = _batch_mean_err(xs[:, k])
+        assert abs(m - exact) < 4 * e + 1e-3, (k, m, exact, e)
+
+
+def test_two_by_two_unconditional_energy_by_transfer_operator():
+    """All four spins free on a 2 x 2 open lattice (a 4-cycle): <e> = -<cos> = -Tr(Kc K^3)/Tr(K^4)."""
+    T = 0.5
+    beta = 1.0 / T
+    x, w = np.polynomial.legendre.leggauss(240)
+    t = np.pi * (x + 1.0)
+    w = np.pi * w
+    D = 0.5 * (t[:, None] - t[None, :])
+    Kw = np.exp(beta * np.cos(D)) * w[None, :]
+    Kcw = np.cos(D) * Kw
+    K2 = Kw @ Kw
+    exact = -np.trace(Kcw @ Kw @ K2) / np.trace(K2 @ K2)
+    gap = np.ones((2, 2), np.uint8)
+    phi = oracle.hot_start(np.zeros((2, 2)), gap, seed=22, img=0, chain=0)
+    es = _mc_series(phi, gap, T, 1.5, 40000, seed=23, fn=lambda p: oracle.energy(p) / 4.0)
+    m, e = _batch_mean_err(es)
+    assert abs(m - exact) < 4 * e + 1e-3, (m, exact, e)
+
+
+def test_fluctuation_relation():
+    """d<e>/dT = N_GP Var(e) / T^2 (canonical identity) against a central difference of e(T)."""
+    L, T, dT = 6, 0.3, 0.03
+    kw = dict(L=L, K=8, n_eq=200, n_meas=4000, seed=24)
+    ep, _ = oracle.e_of_T(T + dT, **kw)
+    em, _ = oracle.e_of_T(T - dT, **kw)
+    _, var = oracle.e_of_T(T, **kw)
+    slope_fd = (ep - em) / (2 * dT)
+    slope_fl = oracle.n_bonds(L, L) * var / T**2
+    assert slope_fl == pytest.approx(slope_fd, rel=0.15)
+
+
+def test_estimate_T_inverts_e_of_T():
+    """SEM: the bisection T reproduces e(T_hat) = e_s within the Monte Carlo error."""
+    kw = dict(L=12, K=4, n_eq=100, n_meas=200, seed=25)
+    T_true = 0.25
+    e_target, _ = oracle.e_of_T(T_true, **kw)
+    T_hat = oracle.estimate_T(e_target, rel_tol=1e-4, **kw)
+    # MC error of e(T): sd(e) ~ 7.7e-3 per sweep, ~4e-4 over 800 correlated sweeps, slope ~0.25
+    assert T_hat == pytest.approx(T_true, rel=0.025)
+    with pytest.raises(ValueError):
+        oracle.estimate_T(-0.3, **kw)  # above the infinite-temperature energy
+    with pytest.raises(ValueError):
+        oracle.estimate_T(-1.01, **kw)  # below the ground state
