@@ -1,0 +1,326 @@
+"""Benchmark: MPR gap site-updates/s of the whole gap-filling job on one GB300.
+
+One step = the whole hot path on one batch (Alg. 2): map + hot start + e_s,
+the specific-energy-matching temperature estimate, n_equil equilibration
+sweeps, n_meas measurement sweeps and the prediction, for the workload
+"4096 x 4096 lognormal GRF, 40% gaps, 32 realisations" (50 + 100 sweeps).
+value = gap site-updates of the step's sweeps / step time (the temperature
+estimate's lattice updates are not counted, its time is).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Several GPUs run independent replicas of the job (realisations are
+independent; there is no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MPR gap site-updates/s at 4096^2 (FP32, batched) and % HBM roofline vs plain path"
+UNIT = "gap site-updates/s"
+WORKLOAD = "lognormal4096_p40: 4096x4096 lognormal GRF (log-mean 5, log-std 1, exponential ell=16), 40% uniform gaps, 32 realisations, 50 equilibration + 100 measurement sweeps"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------ oracle baseline
+
+def _oracle_worker(args):
+    path, chain, sweeps = args
+    import numpy as np
+    import oracle
+    d = np.load(path)
+    phi, g = d["phi"], d["gap"]
+    phi = oracle.hot_start(phi, g, 1, 0, chain)
+    P = int(g.sum())
+    t0 = time.perf_counter()
+    for s in range(sweeps):
+        phi, _ = oracle.sweep(phi, g, T=3e-3, a=1.0 + s / 3.0, seed=1, chain=chain, sweep_index=s)
+    return P * sweeps, time.perf_counter() - t0
+
+
+def cpu_baseline(workers=None, crop=2048, sweeps=1):
+    """The FP64 oracle on the host cores: one sweep of a crop of the input per worker process."""
+    import tempfile
+    import numpy as np
+    import oracle
+    import synthetic
+    oracle.build()
+    workers = workers or min(os.cpu_count() or 1, 16)
+    w = synthetic.workload("lognormal4096")
+    z = w.z[0][:crop, :crop].astype(np.float64)
+    g = w.gap[0][:crop, :crop]
+    phi, _, _ = oracle.map_to_angles(z, g)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "crop.npz")
+        np.savez(path, phi=phi, gap=g)
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(workers) as pool:
+            res = pool.map(_oracle_worker, [(path, c, sweeps) for c in range(workers)])
+        wall = time.perf_counter() - t0
+    units = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": units / busy, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{sweeps} hybrid sweep(s) of a {crop}x{crop} crop of the 4096^2 input, "
+                      f"one realisation per worker, {workers} worker processes "
+                      f"({units} gap site-updates, {wall:.1f} s wall)"}
+
+
+# ------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import synthetic
+    import paper_1710_03038_gb300 as mpr
+    from paper_1710_03038_gb300 import build
+
+    ws, rank, local = _dist()
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    w = synthetic.workload("lognormal4096")
+    z_h, g_h = w.z[0], w.gap[0]
+    R, ne, nm = w.chains, w.n_equil, w.n_meas
+    P = int(g_h.sum())
+    N = g_h.size
+    f = P / N
+    z_d = torch.from_numpy(z_h).to(dev)
+    g_d = torch.from_numpy(g_h).to(dev)
+    z_pin = torch.from_numpy(z_h).pin_memory()
+    g_pin = torch.from_numpy(g_h).pin_memory()
+    params = mpr.Params(seed=12345 + rank, path=args.path)
+    topts = mpr.TOpts()
+    stream = torch.cuda.current_stream(dev)
+
+    sweep_events = []
+
+    def step(z_in, g_in, host_out=None, timed=False):
+        ctx = mpr.Context([z_in], [g_in], chains=R, params=params, topts=topts, device=dev)
+        ctx.estimate_T_async()
+        ctx.sweep(ne, "equil")
+        if timed:
+            for _ in range(nm):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.sweep(1, "measure")
+                e1.record(stream)
+                sweep_events.append((e0, e1))
+        else:
+            ctx.sweep(nm, "measure")
+        if host_out is not None:
+            ctx.predict_host(host_out)
+            out = None
+        else:
+            out = ctx.predict()
+        ctx.close()
+        return out
+
+    for _ in range(args.warmup):
+        step(z_d, g_d)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(z_d, g_d, timed=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = t0.elapsed_time(t1)
+    clocks = clk.stop()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    zh_out = torch.empty(N, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(z_pin, g_pin, host_out=zh_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    units_step = (ne + nm) * P * R
+    value = units_step * args.steps * ws / (ms / 1e3)
+    e2e = units_step * args.steps * ws / (ms_e2e / 1e3)
+    sweep_ms = [a.elapsed_time(b) for a, b in sweep_events]
+    launch_ms = statistics.mean(sweep_ms) / 2.0  # two colour passes per sweep
+    peak, peak_kind = _peaks()
+    alg_bytes_per_update = 4.0 * (1.0 / f + 1.0)
+    achieved = (P * R / 2.0) * alg_bytes_per_update / (launch_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "impl": "gb300",
+        "config": {"workload": WORKLOAD, "path": args.path, "image": [4096, 4096],
+                   "gap_fraction": round(f, 6), "realisations": R, "n_equil": ne, "n_meas": nm,
+                   "T_estimate": {"L": 256, "chains": topts.chains, "iters": topts.iters,
+                                  "n_equil": topts.n_equil, "n_meas": topts.n_meas},
+                   "l2": "inputs larger than L2 (state 2.1 GB)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "tiled_pass_kernel" if args.path == "tiled" else "plain_pass_kernel",
+                     "alg_bytes_per_gap_update": alg_bytes_per_update,
+                     "avg_launch_ms": launch_ms, "peak_kind": peak_kind},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N * 5,
+                "d2h_bytes_per_step": N * 4},
+        "clocks": clocks,
+    }
+    # kernel launches of one step: 3 per sweep (two colour passes + bookkeeping) for the
+    # main chains and for the temperature lattices, plus the fixed init/predict kernels
+    t_sweeps = topts.iters * (topts.n_equil + topts.n_meas) + topts.n_equil
+    line["gpu_launches"] = args.steps * (3 * (ne + nm) + 3 * t_sweeps + topts.iters + 1 + 14)
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import synthetic
+    w = synthetic.workload("lognormal4096")
+    times, units = [], 0
+    cb = None
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(crop=1024)
+        if k >= args.warmup:
+            times.append(cb["value"])
+    value = statistics.mean(times)
+    P = int(w.gap[0].sum())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample": "oracle sweeps on crops of the input"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gap_sites": P,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--path", default="tiled", choices=["tiled", "plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * mpr.h -- C ABI of the GB300 library for gap filling with the modified
+ * planar rotator (MPR) Gibbs Markov random field (Zukovic & Hristopulos,
+ * arXiv:1710.03038).
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an mpr_status (MPR_OK = 0) and never throws.
+ *    mpr_last_error() returns a static, thread-local description of the last
+ *    failure in the calling thread.
+ *  - Device buffers are owned by the caller.  The library allocates no
+ *    device memory: the caller queries mpr_workspace_size(), allocates one
+ *    device workspace and passes it to mpr_init_grid(); the context keeps
+ *    pointers into it and only a small host-side descriptor of its own.
+ *  - Functions taking an mpr_stream enqueue their work on that stream and
+ *    return without waiting unless stated otherwise ("blocking").  Outputs
+ *    written to device memory are valid once the stream has reached that
+ *    point.  Host outputs are written before the function returns.
+ *  - Image data are passed as the row-major images concatenated in order:
+ *    image i starts at element sum_{k<i} Lx[k] * Ly[k].
+ *  - Angles are single precision radians; energies and temperatures are
+ *    double precision.
+ *  - An mpr_ctx is not thread safe; distinct contexts are independent.
+ */
+#ifndef MPR_H
+#define MPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mpr_status;
+#define MPR_OK                   0
+#define MPR_ERR_INVALID_ARG      1  /* null pointer, bad size or flag            */
+#define MPR_ERR_CUDA             2  /* a CUDA runtime call failed                */
+#define MPR_ERR_DEGENERATE_RANGE 3  /* an image has z_max == z_min over samples  */
+#define MPR_ERR_NO_SAMPLE_PAIRS  4  /* no sample-sample bond: e_s undefined      */
+#define MPR_ERR_T_OUT_OF_RANGE   5  /* e_s outside (-J, -4J/pi^2)                 */
+#define MPR_ERR_WORKSPACE        6  /* workspace missing, misaligned or too small */
+#define MPR_ERR_STATE            7  /* call not valid in the context's state      */
+#define MPR_ERR_DEVICE           8  /* a kernel reported an error (status word)   */
+
+/* A CUDA stream (binary compatible with cudaStream_t); NULL = legacy stream. */
+typedef struct CUstream_st* mpr_stream;
+
+typedef struct mpr_ctx mpr_ctx;
+
+/* Where a user buffer lives. */
+typedef enum { MPR_DEVICE = 0, MPR_HOST = 1 } mpr_mem;
+
+/* Kernel family used by a context. */
+typedef enum {
+    MPR_PATH_TILED = 0,  /* batched: compact gap state, tile-major, chain-inner loop */
+    MPR_PATH_PLAIN = 1   /* dense per-chain planes, one thread per site, two passes  */
+} mpr_path;
+
+/* Sweep phases of Alg. 2: equilibration (step 4, a adapted) and sampling
+ * (step 5, a frozen, realisations accumulated). */
+typedef enum { MPR_EQUIL = 0, MPR_MEASURE = 1 } mpr_phase;
+
+/* Flags of mpr_sweep. */
+#define MPR_RECORD_ENERGY 1  /* reduce H / N_GP of every chain after every sweep (Alg. 2 step 4.3) */
+
+/* Model and simulation parameters (Sec. 2.2, 2.5).  mpr_default_params()
+ * fills the paper's values. */
+typedef struct {
+    double q;                /* modification factor of Eq. Hamiltonian_mod, 0 < q <= 1/2; 0.5 */
+    double J;                /* exchange interaction J > 0; 1                                  */
+    double A_targ;           /* target acceptance ratio of Alg. 2 step 4.2; 0.3                */
+    double k_a;              /* rate of the perturbation control factor a; 3                   */
+    uint64_t seed;           /* Philox key (64 bits)                                           */
+    int freeze_a_in_measure; /* 1: keep the last equilibration a while sampling; 0: a = 1
+                                as printed in Alg. 2 step 5.2                                   */
+    int path;                /* mpr_path                                                       */
+    int tile_x, tile_y;      /* tiled path tile shape; 0 = autotuned                          */
+    int chain_group;         /* tiled path: chains per thread block; 0 = autotuned            */
+} mpr_params;
+
+/* Options of the specific-energy-matching temperature estimate (Sec. 2.3). */
+typedef struct {
+    int L;                 /* side of the unconditional lattice for e(T); 0: min(256, image side) */
+    int chains;            /* independent unconditional chains per image; 4                      */
+    int n_equil;           /* sweeps after each temperature change; 60                           */
+    int n_meas;            /* sweeps averaged for <e> and Var(e) per iteration; 120              */
+    int iters;             /* Newton iterations; 6                                               */
+    double T_lo, T_hi;     /* safeguarding bracket; 1e-5, 20                                      */
+} mpr_T_opts;
+
+const char* mpr_version(void);
+const char* mpr_last_error(void);
+const char* mpr_status_string(mpr_status s);
+
+mpr_status mpr_default_params(mpr_params* p);
+mpr_status mpr_default_T_opts(mpr_T_opts* o);
+
+/* Bytes of device workspace a context needs (Sec. 2.5 state: angles of every
+ * realisation, accumulators, tile tables, the unconditional lattices of the
+ * temperature estimate and input/output staging).
+ *  n_img       number of images, >= 1
+ *  Lx, Ly      host [n_img] image sizes, 2 <= Lx <= 65535, 2 <= Ly <= 65535
+ *  n_gap       host [n_img] number of missing pixels per image, or NULL to
+ *              size for the worst case (every pixel missing)
+ *  n_chains    realisations per image, >= 1
+ *  p, T_opts   the parameters the context will use (T_opts may be NULL for
+ *              the defaults)
+ *  bytes       out: required size; the workspace must be 256-byte aligned. */
+mpr_status mpr_workspace_size(int n_img, const int* Lx, const int* Ly, const int64_t* n_gap,
+                              int n_chains, const mpr_params* p, const mpr_T_opts* T_opts,
+                              size_t* bytes);
+
+/* Alg. 2 steps 1-2 and 3.1 for a batch of images: maps the sample values to
+ * angles with Eq. map (extremes over sample sites), builds the gap layout,
+ * draws the hot start of every realisation (gap angles ~ U(0, 2 pi), step
+ * 1.8), sets a = 1, and computes the sample specific energy e_s of
+ * Eq. mpr-sse (mean over unordered sample-sample bonds, FP64).
+ *  z       [sum Lx*Ly] float values; entries at gap pixels are ignored
+ *  gap     [sum Lx*Ly] uint8, nonzero = missing
+ *  where   whether z and gap are host or device pointers
+ *  workspace, ws_bytes  caller-owned device memory of mpr_workspace_size() bytes
+ * Blocking.  Errors: INVALID_ARG, WORKSPACE (too small for the actual gap
+ * counts), DEGENERATE_RANGE (fewer than two distinct sample values).
+ * On success *out owns no device memory; release it with mpr_destroy(). */
+mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly, int n_chains,
+                         const mpr_params* p, const mpr_T_opts* T_opts,
+                         const float* z, const uint8_t* gap, mpr_mem where,
+                         void* workspace, size_t ws_bytes, mpr_stream stream);
+
+/* Host copy of what init computed per image: e_s (nan when N_SP = 0), N_SP,
+ * P (gap count), z_min, z_max.  Any pointer may be NULL. */
+mpr_status mpr_get_image_info(const mpr_ctx* ctx, double* e_s, int64_t* n_sp, int64_t* n_gap,
+                              float* z_min, float* z_max);
+
+/* Specific energy matching (Sec. 2.3, Alg. 2 step 3): for every image finds
+ * T with e(T, L_T) = e_s, where e(T, L_T) = <H>/N_GP of an unconditional
+ * simulation on an L_T x L_T lattice.  Newton iterations on the device use
+ * the fluctuation relation d<e>/dT = N_GP Var(e) / T^2, safeguarded by a
+ * bracket; every iteration re-equilibrates the lattices (warm start) and
+ * averages n_meas sweeps over all chains.  The result becomes the context's
+ * temperature.  T_out: host [n_img] (blocking) or NULL (asynchronous).
+ * Errors: NO_SAMPLE_PAIRS, T_OUT_OF_RANGE (e_s >= -4J/pi^2 or <= -J). */
+mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_out, mpr_stream stream);
+
+/* Sets / reads the reduced temperature of every image (host [n_img]). */
+mpr_status mpr_set_T(mpr_ctx* ctx, const double* T, mpr_stream stream);
+mpr_status mpr_get_T(mpr_ctx* ctx, double* T, mpr_stream stream);
+
+/* n_sweeps hybrid sweeps (Alg. 1) of every realisation on the red/black
+ * checkerboard (red = (x + y) even first).  Each gap site gets the
+ * over-relaxation reflection (Eq. over-relax, q-consistent), then the
+ * restricted Metropolis proposal phi'' = (phi' + 2 pi (u - 1/2)/a) mod 2 pi
+ * accepted with probability min(1, exp(-dH/T)).  phase MPR_EQUIL applies
+ * Alg. 2 step 4.2 after every sweep (a <- 1 + (i+1)/k_a when the chain's
+ * acceptance ratio is below A_targ, i the equilibration sweep index);
+ * MPR_MEASURE keeps a and adds every sweep's angles to the realisation
+ * accumulators (Alg. 2 step 5).  flags: MPR_RECORD_ENERGY.  Asynchronous. */
+mpr_status mpr_sweep(mpr_ctx* ctx, int n_sweeps, int phase, int flags, mpr_stream stream);
+
+/* Specific energy H/N_GP (Eq. ene, FP64) of every realisation in its current
+ * state, e_out [n_img * n_chains] (image-major) on the host (blocking) or the
+ * device (asynchronous). */
+mpr_status mpr_energy(mpr_ctx* ctx, double* e_out, mpr_mem where, mpr_stream stream);
+
+/* Prediction = conditional mean over realisations (Sec. 3; Alg. 2 steps
+ * 5.3 and 6): for gap pixels z_min + (z_max - z_min) * mean(phi) / (2 pi),
+ * the mean over every chain and every measurement sweep; sample pixels
+ * return their value.  z_std (nullable) receives the standard deviation of
+ * the back-transformed realisations (0 at samples).  Both [sum Lx*Ly] on
+ * the host (blocking) or the device.  Error STATE if no measurement sweep ran. */
+mpr_status mpr_predict(mpr_ctx* ctx, float* z_hat, float* z_std, mpr_mem where,
+                       mpr_stream stream);
+
+/* Clears the realisation accumulators (keeps the chains' states). */
+mpr_status mpr_reset_accumulators(mpr_ctx* ctx, mpr_stream stream);
+
+/* Checkpoint / parity access to the full simulation state.
+ * phi: [sum over images of n_chains * Lx * Ly] floats, image-major then
+ * chain-major, row-major; get writes sample pixels with their fixed angles,
+ * set reads only gap pixels.  Device or host (blocking). */
+mpr_status mpr_get_state(mpr_ctx* ctx, float* phi, mpr_mem where, mpr_stream stream);
+mpr_status mpr_set_state(mpr_ctx* ctx, const float* phi, mpr_mem where, mpr_stream stream);
+
+/* Per realisation (image-major, [n_img * n_chains], host, blocking): the
+ * perturbation control factor a, the accepted proposals of the last sweep
+ * and the specific energy recorded after the last sweep (nan if the last
+ * sweep did not record it).  Any pointer may be NULL. */
+mpr_status mpr_get_chain_info(mpr_ctx* ctx, float* a, uint32_t* accepted, double* e_last,
+                              mpr_stream stream);
+/* Overwrites a per realisation (host [n_img * n_chains]). */
+mpr_status mpr_set_chain_a(mpr_ctx* ctx, const float* a, mpr_stream stream);
+
+/* Sweep counter that keys the random stream (sweep field of the Philox
+ * counter) and the equilibration index i of Alg. 2 step 4.2. */
+mpr_status mpr_get_sweep_index(const mpr_ctx* ctx, uint32_t* sweep, uint32_t* equil_index);
+mpr_status mpr_set_sweep_index(mpr_ctx* ctx, uint32_t sweep, uint32_t equil_index,
+                               mpr_stream stream);
+
+/* Releases the host descriptor.  The workspace stays the caller's. */
+void mpr_destroy(mpr_ctx* ctx);
+
+/* ---- context-free kernels ---------------------------------------------- */
+
+/* Energy of Eq. Hamiltonian_mod on n dense angle grids (device, row-major,
+ * grid k at offset sum_{j<k} Lx[j]*Ly[j]; open boundaries): H_out device
+ * [n] FP64.  Lx, Ly host [n].  Asynchronous. */
+mpr_status mpr_lattice_energy(int n, const int* Lx, const int* Ly, const float* phi,
+                              double q, double J, double* H_out, mpr_stream stream);
+
+/* Gradient of the same energy: grad_i = g_k * J q sum_j sin(q (phi_i - phi_j))
+ * for site i of grid k, with g device [n] FP64 upstream weights (dL/dH_k).
+ * grad device, same layout as phi.  (dH/dJ = H/J needs no kernel.) */
+mpr_status mpr_lattice_torque(int n, const int* Lx, const int* Ly, const float* phi,
+                              double q, double J, const double* g, float* grad,
+                              mpr_stream stream);
+
+/* Philox4x32-10 blocks of the library's random stream for n counters
+ * (device uint32 [4n] in, [4n] out; key host [2]).  reference != 0 runs the
+ * CUDA toolkit's own Philox4x32-10 device routine instead, for
+ * cross-checking.  Asynchronous. */
+mpr_status mpr_philox(int n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                      int reference, mpr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPR_H */

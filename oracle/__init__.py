@@ -63,6 +63,8 @@ def _load():
             "oracle_torque": (None, [i, i, dp, d, d, dp]),
             "oracle_over_relax": (d, [d, dp, i, d, i, C.POINTER(d), C.POINTER(d)]),
             "oracle_sweep": (lng, [i, i, dp, u8, d, d, d, d, u64, u32s, u32s, u32s, i, dpn]),
+            "oracle_site_update": (d, [d, dp, i, d, d, d, d, u64, u32s, u32s, u32s, i, i, i, i,
+                                       C.POINTER(i), dpn]),
             "oracle_adapt_a": (d, [d, lng, lng, lng, d, d]),
             "oracle_e_of_T": (d, [i, i, i, i, d, d, d, d, d, u64, u32s, C.POINTER(d)]),
             "oracle_estimate_T": (i, [d, i, i, i, i, d, d, d, d, u64, u32s, d, d, d, i,
@@ -192,6 +194,18 @@ def sweep(phi, gap, *, T, a, seed, img=0, chain=0, sweep_index=0, q=0.5, J=1.0,
     if diagnostics:
         return p, int(n_acc), {k: d[..., j] for j, k in enumerate(DIAG_FIELDS)}
     return p, int(n_acc)
+
+
+def site_update(phi, nbr, *, x, y, T, a, seed, img=0, chain=0, sweep_index=0, q=0.5, J=1.0,
+                literal_or=False):
+    """Alg. 1 on one site with neighbour angles nbr -> (phi_new, accepted, diag dict)."""
+    nb = _f64(nbr)
+    acc = C.c_int()
+    d = np.zeros(len(DIAG_FIELDS))
+    out = _load().oracle_site_update(float(phi), nb, nb.size, q, J, T, a, seed, img, chain,
+                                     sweep_index, int(x), int(y), (int(x) + int(y)) & 1,
+                                     int(literal_or), C.byref(acc), _ptr(d))
+    return out, bool(acc.value), dict(zip(DIAG_FIELDS, d))
 
 
 def adapt_a(a, n_acc, n_gap, i, A_targ=0.3, k_a=3.0):

@@ -236,12 +236,47 @@ static double site_energy(double v, const double* nbr, int n, double q, double J
  * sensitivity of dH/T to a unit angle error, accepted flag. */
 enum { D_RMAP = 0, D_AP, D_DHT, D_ORSLACK, D_WRAPSLACK, D_FIELD, D_SENS, D_ACC, D_N };
 
+/* Alg. 1 applied to one gap site (x, y) of colour `colour` whose current
+ * angle is phi and whose n existing neighbours hold nbr[0..n-1]: the
+ * over-relaxation step, then the restricted Metropolis step
+ * phi'' = (phi' + 2 pi (u - 1/2) / a) mod 2 pi, accepted iff
+ * r < min(1, exp(-dH / T)) (ties reject).  Returns the new angle; *acc
+ * receives 1 if the proposal was accepted; d (nullable) the D_N diagnostics. */
+double oracle_site_update(double phi, const double* nbr, int n, double q, double J, double T,
+                          double a, uint64_t seed, uint32_t img, uint32_t chain, uint32_t sweep,
+                          int x, int y, int colour, int literal_or, int* acc, double* d)
+{
+    double or_slack, field;
+    double p1 = oracle_over_relax(phi, nbr, n, q, literal_or, &or_slack, &field);
+    double u, r;
+    site_uniforms(seed, img, chain, sweep, x, y, colour, &u, &r);
+    double raw = p1 + (OR_TWO_PI / a) * (u - 0.5);
+    double p2 = mod_two_pi(raw);
+    double dH = site_energy(p2, nbr, n, q, J) - site_energy(p1, nbr, n, q, J);
+    double ap = dH <= 0.0 ? 1.0 : exp(-dH / T);
+    int ok = r < ap;
+    if (d) {
+        double sens = 0.0;
+        for (int j = 0; j < n; ++j)
+            sens += fabs(sin(q * (p2 - nbr[j]))) + fabs(sin(q * (p1 - nbr[j])));
+        double w0 = fabs(raw), w1 = fabs(raw - OR_TWO_PI);
+        d[D_RMAP] = r - ap;
+        d[D_AP] = ap;
+        d[D_DHT] = dH / T;
+        d[D_ORSLACK] = or_slack;
+        d[D_WRAPSLACK] = w0 < w1 ? w0 : w1;
+        d[D_FIELD] = field;
+        d[D_SENS] = J * q * sens / T;
+        d[D_ACC] = ok;
+    }
+    *acc = ok;
+    return ok ? p2 : p1;
+}
+
 /* One hybrid sweep (Alg. 1) on the red/black checkerboard: colour 0
  * ((x + y) even) first, then colour 1; within a colour every gap site in
- * row-major order.  Each gap site gets the over-relaxation step, then the
- * restricted Metropolis step phi'' = (phi' + 2 pi (u - 1/2) / a) mod 2 pi,
- * accepted iff r < min(1, exp(-dH / T)) (ties reject).  Returns the number of
- * accepted proposals. */
+ * row-major order gets oracle_site_update().  Returns the number of accepted
+ * proposals. */
 long oracle_sweep(int Lx, int Ly, double* phi, const uint8_t* gap,
                   double q, double J, double T, double a,
                   uint64_t seed, uint32_t img, uint32_t chain, uint32_t sweep,
@@ -258,31 +293,10 @@ long oracle_sweep(int Lx, int Ly, double* phi, const uint8_t* gap,
                 if (!gap[i]) continue;
                 int n = neighbours(Lx, Ly, x, y, nb);
                 for (int j = 0; j < n; ++j) nbr[j] = phi[nb[j]];
-                double or_slack, field;
-                double p1 = oracle_over_relax(phi[i], nbr, n, q, literal_or, &or_slack, &field);
-                double u, r;
-                site_uniforms(seed, img, chain, sweep, x, y, colour, &u, &r);
-                double raw = p1 + (OR_TWO_PI / a) * (u - 0.5);
-                double p2 = mod_two_pi(raw);
-                double dH = site_energy(p2, nbr, n, q, J) - site_energy(p1, nbr, n, q, J);
-                double ap = dH <= 0.0 ? 1.0 : exp(-dH / T);
-                int acc = r < ap;
-                if (diag) {
-                    double* d = diag + (long)D_N * i;
-                    double sens = 0.0;
-                    for (int j = 0; j < n; ++j)
-                        sens += fabs(sin(q * (p2 - nbr[j]))) + fabs(sin(q * (p1 - nbr[j])));
-                    double w0 = fabs(raw), w1 = fabs(raw - OR_TWO_PI);
-                    d[D_RMAP] = r - ap;
-                    d[D_AP] = ap;
-                    d[D_DHT] = dH / T;
-                    d[D_ORSLACK] = or_slack;
-                    d[D_WRAPSLACK] = w0 < w1 ? w0 : w1;
-                    d[D_FIELD] = field;
-                    d[D_SENS] = J * q * sens / T;
-                    d[D_ACC] = acc;
-                }
-                phi[i] = acc ? p2 : p1;
+                int acc;
+                phi[i] = oracle_site_update(phi[i], nbr, n, q, J, T, a, seed, img, chain, sweep,
+                                            x, y, colour, literal_or, &acc,
+                                            diag ? diag + (long)D_N * i : NULL);
                 n_acc += acc;
             }
     return n_acc;

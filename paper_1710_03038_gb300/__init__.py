@@ -1,0 +1,354 @@
+"""GB300-native gap filling with the modified planar rotator (MPR) Gibbs random field.
+
+Thin Python layer over the C ABI of ``include/mpr.h``: it owns device memory
+(torch tensors) and streams and marshals arguments; every step of the method
+runs in the library's CUDA kernels.
+
+    ctx = Context([z], [gap], chains=32)      # Alg. 2 steps 1-3.1
+    ctx.estimate_T()                           # Sec. 2.3, specific energy matching
+    ctx.sweep(50, "equil")                     # Alg. 2 step 4
+    ctx.sweep(100, "measure")                  # Alg. 2 step 5
+    z_hat = ctx.predict()                      # conditional mean
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MprParams, MprTOpts, call, int_array, i64_array
+
+__all__ = ["Params", "TOpts", "Context", "fill", "MPREnergy", "lattice_energy", "lattice_torque",
+           "philox", "version", "workspace_size"]
+
+
+def version() -> str:
+    return _lib.load().mpr_version().decode()
+
+
+@dataclass
+class Params:
+    """Model and simulation parameters (defaults: the paper's values)."""
+    q: float = 0.5
+    J: float = 1.0
+    A_targ: float = 0.3
+    k_a: float = 3.0
+    seed: int = 0x2545F4914F6CDD1D
+    freeze_a_in_measure: bool = True
+    path: str = "tiled"          # "tiled" (batched) or "plain"
+    tile: tuple = (0, 0)         # (tile_x, tile_y); (0, 0) = automatic
+    chain_group: int = 0         # chains per thread block; 0 = automatic
+
+    def c(self) -> MprParams:
+        p = MprParams()
+        call("mpr_default_params", C.byref(p))
+        p.q, p.J, p.A_targ, p.k_a = self.q, self.J, self.A_targ, self.k_a
+        p.seed = int(self.seed) & ((1 << 64) - 1)
+        p.freeze_a_in_measure = int(bool(self.freeze_a_in_measure))
+        p.path = {"tiled": _lib.MPR_PATH_TILED, "plain": _lib.MPR_PATH_PLAIN}[self.path]
+        p.tile_x, p.tile_y = int(self.tile[0]), int(self.tile[1])
+        p.chain_group = int(self.chain_group)
+        return p
+
+
+@dataclass
+class TOpts:
+    """Options of the temperature estimate (unconditional lattice side, chains, sweeps)."""
+    L: int = 0
+    chains: int = 4
+    n_equil: int = 60
+    n_meas: int = 120
+    iters: int = 6
+    T_lo: float = 1e-5
+    T_hi: float = 20.0
+
+    def c(self) -> MprTOpts:
+        o = MprTOpts()
+        o.L, o.chains, o.n_equil, o.n_meas, o.iters = (int(self.L), int(self.chains),
+                                                       int(self.n_equil), int(self.n_meas),
+                                                       int(self.iters))
+        o.T_lo, o.T_hi = float(self.T_lo), float(self.T_hi)
+        return o
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _as_list(x):
+    if isinstance(x, (list, tuple)):
+        return list(x)
+    if isinstance(x, torch.Tensor) and x.dim() == 2:
+        return [x]
+    if isinstance(x, np.ndarray) and x.ndim == 2:
+        return [x]
+    return list(x)
+
+
+def workspace_size(shapes, n_gap, chains, params: Params = None, topts: TOpts = None) -> int:
+    params = params or Params()
+    topts = topts or TOpts()
+    n = len(shapes)
+    Ly = int_array([s[0] for s in shapes])
+    Lx = int_array([s[1] for s in shapes])
+    ng = i64_array(n_gap) if n_gap is not None else None
+    out = C.c_size_t()
+    call("mpr_workspace_size", n, Lx, Ly, ng, int(chains), C.byref(params.c()),
+         C.byref(topts.c()), C.byref(out))
+    return out.value
+
+
+class Context:
+    """A batch of gappy images and their realisations on one GPU (an mpr_ctx).
+
+    z, gap: sequences of 2-D arrays (numpy, or torch tensors on the host or on
+    the current CUDA device); gap nonzero = missing.  Inputs on the host are
+    copied by the library (``where="host"``), device tensors are read in
+    place.
+    """
+
+    def __init__(self, z, gap, chains: int, params: Params = None, topts: TOpts = None,
+                 device=None, stream=None):
+        self.params = params or Params()
+        self.topts = topts or TOpts()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        zs = _as_list(z)
+        gs = _as_list(gap)
+        if len(zs) != len(gs):
+            raise ValueError("z and gap must have the same number of images")
+        self.shapes = [tuple(int(v) for v in g.shape) for g in gs]
+        self.n_img = len(self.shapes)
+        self.chains = int(chains)
+        on_dev = isinstance(zs[0], torch.Tensor) and zs[0].is_cuda
+        if on_dev:
+            zf = torch.cat([t.reshape(-1).to(torch.float32) for t in zs]).contiguous()
+            gf = torch.cat([(t.reshape(-1) != 0).to(torch.uint8) for t in gs]).contiguous()
+            where = _lib.MPR_DEVICE
+            ng = [int(g.count_nonzero()) for g in gs]
+        else:
+            zn = [np.asarray(t.cpu() if isinstance(t, torch.Tensor) else t, dtype=np.float32) for t in zs]
+            gn = [(np.asarray(t.cpu() if isinstance(t, torch.Tensor) else t) != 0).astype(np.uint8) for t in gs]
+            zf = torch.from_numpy(np.concatenate([a.ravel() for a in zn])).pin_memory()
+            gf = torch.from_numpy(np.concatenate([a.ravel() for a in gn])).pin_memory()
+            where = _lib.MPR_HOST
+            ng = [int(a.sum()) for a in gn]
+        self.n_sites = int(sum(a * b for a, b in self.shapes))
+        Ly = int_array([s[0] for s in self.shapes])
+        Lx = int_array([s[1] for s in self.shapes])
+        cp, co = self.params.c(), self.topts.c()
+        nbytes = C.c_size_t()
+        call("mpr_workspace_size", self.n_img, Lx, Ly, i64_array(ng), self.chains, C.byref(cp),
+             C.byref(co), C.byref(nbytes))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self._ctx = C.c_void_p()
+        call("mpr_init_grid", C.byref(self._ctx), self.n_img, Lx, Ly, self.chains, C.byref(cp),
+             C.byref(co), _ptr(zf), _ptr(gf), where, _ptr(self.workspace),
+             C.c_size_t(self.workspace.numel()), _stream_ptr(stream))
+        self._inputs = (zf, gf)
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            _lib.load().mpr_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- info --------------------------------------------------------------
+    def image_info(self) -> dict:
+        n = self.n_img
+        e_s = (C.c_double * n)()
+        nsp = (C.c_int64 * n)()
+        ngap = (C.c_int64 * n)()
+        zmin = (C.c_float * n)()
+        zmax = (C.c_float * n)()
+        call("mpr_get_image_info", self._ctx, e_s, nsp, ngap, zmin, zmax)
+        return dict(e_s=np.array(e_s[:]), n_sp=np.array(nsp[:]), n_gap=np.array(ngap[:]),
+                    zmin=np.array(zmin[:]), zmax=np.array(zmax[:]))
+
+    # -- temperature -----------------------------------------------------------
+    def estimate_T(self, stream=None) -> np.ndarray:
+        T = (C.c_double * self.n_img)()
+        call("mpr_estimate_T", self._ctx, T, _stream_ptr(stream))
+        return np.array(T[:])
+
+    def estimate_T_async(self, stream=None):
+        call("mpr_estimate_T", self._ctx, None, _stream_ptr(stream))
+
+    def set_T(self, T, stream=None):
+        T = np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_img,))
+        call("mpr_set_T", self._ctx, (C.c_double * self.n_img)(*T), _stream_ptr(stream))
+
+    def get_T(self, stream=None) -> np.ndarray:
+        T = (C.c_double * self.n_img)()
+        call("mpr_get_T", self._ctx, T, _stream_ptr(stream))
+        return np.array(T[:])
+
+    # -- sweeps ----------------------------------------------------------------
+    def sweep(self, n: int, phase: str = "equil", record_energy: bool = False, stream=None):
+        ph = {"equil": _lib.MPR_EQUIL, "measure": _lib.MPR_MEASURE}[phase]
+        call("mpr_sweep", self._ctx, int(n), ph, _lib.MPR_RECORD_ENERGY if record_energy else 0,
+             _stream_ptr(stream))
+
+    def energy(self, stream=None) -> np.ndarray:
+        out = (C.c_double * (self.n_img * self.chains))()
+        call("mpr_energy", self._ctx, C.cast(out, C.c_void_p), _lib.MPR_HOST, _stream_ptr(stream))
+        return np.array(out[:]).reshape(self.n_img, self.chains)
+
+    def predict(self, std: bool = False, stream=None):
+        """Conditional mean (and std) per image as device tensors."""
+        zh = torch.empty(self.n_sites, dtype=torch.float32, device=self.device)
+        zs = torch.empty(self.n_sites, dtype=torch.float32, device=self.device) if std else None
+        call("mpr_predict", self._ctx, _ptr(zh), _ptr(zs) if std else None, _lib.MPR_DEVICE,
+             _stream_ptr(stream))
+        out = self._split(zh)
+        return (out, self._split(zs)) if std else out
+
+    def predict_host(self, out: torch.Tensor, std_out: torch.Tensor = None, stream=None):
+        """Conditional mean into a (pinned) host buffer of n_sites floats; blocking."""
+        call("mpr_predict", self._ctx, _ptr(out), _ptr(std_out) if std_out is not None else None,
+             _lib.MPR_HOST, _stream_ptr(stream))
+
+    def reset_accumulators(self, stream=None):
+        call("mpr_reset_accumulators", self._ctx, _stream_ptr(stream))
+
+    def _split(self, flat):
+        out, off = [], 0
+        for (h, w) in self.shapes:
+            out.append(flat[off:off + h * w].view(h, w))
+            off += h * w
+        return out
+
+    # -- state -------------------------------------------------------------------
+    def get_state(self, stream=None):
+        """Angles of every realisation: list per image of [chains, Ly, Lx] device tensors."""
+        flat = torch.empty(self.n_sites * self.chains, dtype=torch.float32, device=self.device)
+        call("mpr_get_state", self._ctx, _ptr(flat), _lib.MPR_DEVICE, _stream_ptr(stream))
+        out, off = [], 0
+        for (h, w) in self.shapes:
+            n = h * w * self.chains
+            out.append(flat[off:off + n].view(self.chains, h, w))
+            off += n
+        return out
+
+    def set_state(self, states, stream=None):
+        flat = torch.cat([torch.as_tensor(s, dtype=torch.float32, device=self.device).reshape(-1)
+                          for s in _as_list(states)]).contiguous()
+        if flat.numel() != self.n_sites * self.chains:
+            raise ValueError("state has the wrong size")
+        call("mpr_set_state", self._ctx, _ptr(flat), _lib.MPR_DEVICE, _stream_ptr(stream))
+        torch.cuda.current_stream().synchronize()
+
+    def chain_info(self, stream=None) -> dict:
+        n = self.n_img * self.chains
+        a = (C.c_float * n)()
+        acc = (C.c_uint32 * n)()
+        e = (C.c_double * n)()
+        call("mpr_get_chain_info", self._ctx, a, acc, e, _stream_ptr(stream))
+        shp = (self.n_img, self.chains)
+        return dict(a=np.array(a[:]).reshape(shp), accepted=np.array(acc[:]).reshape(shp),
+                    e_last=np.array(e[:]).reshape(shp))
+
+    def set_chain_a(self, a, stream=None):
+        a = np.broadcast_to(np.asarray(a, dtype=np.float32), (self.n_img * self.chains,)).copy()
+        call("mpr_set_chain_a", self._ctx, a.ctypes.data_as(C.POINTER(C.c_float)), _stream_ptr(stream))
+
+    def sweep_index(self):
+        s, e = C.c_uint32(), C.c_uint32()
+        call("mpr_get_sweep_index", self._ctx, C.byref(s), C.byref(e))
+        return s.value, e.value
+
+    def set_sweep_index(self, sweep: int, equil_index: int, stream=None):
+        call("mpr_set_sweep_index", self._ctx, C.c_uint32(sweep), C.c_uint32(equil_index),
+             _stream_ptr(stream))
+
+
+def fill(z, gap, chains: int, n_equil: int, n_meas: int, params: Params = None,
+         topts: TOpts = None, T=None, std: bool = False):
+    """Whole gap fill (Alg. 2): init, SEM temperature (unless T given), sweeps, prediction."""
+    ctx = Context(z, gap, chains, params, topts)
+    if T is None:
+        ctx.estimate_T_async()
+    else:
+        ctx.set_T(T)
+    ctx.sweep(n_equil, "equil")
+    ctx.sweep(n_meas, "measure")
+    out = ctx.predict(std=std)
+    return out, ctx
+
+
+# ---------------------------------------------------------------- energy autograd
+
+def lattice_energy(phi: torch.Tensor, q: float = 0.5, J: float = 1.0, stream=None) -> torch.Tensor:
+    """H (FP64) of a [..., Ly, Lx] float32 CUDA tensor of angles, one value per leading index."""
+    Ly, Lx = phi.shape[-2:]
+    n = int(np.prod(phi.shape[:-2])) if phi.dim() > 2 else 1
+    p = phi.contiguous()
+    H = torch.empty(n, dtype=torch.float64, device=phi.device)
+    call("mpr_lattice_energy", n, int_array([Lx] * n), int_array([Ly] * n), _ptr(p), float(q),
+         float(J), _ptr(H), _stream_ptr(stream))
+    return H.reshape(phi.shape[:-2])
+
+
+def lattice_torque(phi: torch.Tensor, g: torch.Tensor, q: float = 0.5, J: float = 1.0,
+                   stream=None) -> torch.Tensor:
+    """g_k * dH_k/dphi for a [..., Ly, Lx] float32 CUDA tensor (g: FP64 weights per grid)."""
+    Ly, Lx = phi.shape[-2:]
+    n = int(np.prod(phi.shape[:-2])) if phi.dim() > 2 else 1
+    p = phi.contiguous()
+    gg = g.reshape(-1).to(torch.float64).contiguous()
+    grad = torch.empty_like(p)
+    call("mpr_lattice_torque", n, int_array([Lx] * n), int_array([Ly] * n), _ptr(p), float(q),
+         float(J), _ptr(gg), _ptr(grad), _stream_ptr(stream))
+    return grad
+
+
+class MPREnergy(torch.autograd.Function):
+    """H(phi, J) = -J sum_<ij> cos(q (phi_i - phi_j)) with a hand-written backward.
+
+    forward returns H per grid (FP64); backward returns the torque
+    dH/dphi_i = J q sum_j sin(q (phi_i - phi_j)) times the upstream gradient,
+    and dH/dJ = H / J.
+    """
+
+    @staticmethod
+    def forward(ctx, phi, J, q=0.5):
+        Jv = float(J.item()) if isinstance(J, torch.Tensor) else float(J)
+        H = lattice_energy(phi, q=q, J=Jv)
+        ctx.save_for_backward(phi, H)
+        ctx.q = q
+        ctx.J = Jv
+        ctx.J_is_tensor = isinstance(J, torch.Tensor)
+        return H
+
+    @staticmethod
+    def backward(ctx, gH):
+        phi, H = ctx.saved_tensors
+        g_phi = lattice_torque(phi, gH.to(torch.float64), q=ctx.q, J=ctx.J)
+        g_J = None
+        if ctx.J_is_tensor:
+            g_J = (gH.to(torch.float64) * H / ctx.J).sum().to(torch.float64)
+        return g_phi, g_J, None
+
+
+def philox(ctr: np.ndarray, key, reference: bool = False) -> np.ndarray:
+    """Philox4x32-10 blocks computed on the GPU (reference=True: the CUDA toolkit's routine)."""
+    c = torch.as_tensor(np.ascontiguousarray(ctr, dtype=np.uint32).view(np.int32), device="cuda")
+    out = torch.empty_like(c)
+    k = (C.c_uint32 * 2)(int(key[0]), int(key[1]))
+    n = c.numel() // 4
+    call("mpr_philox", n, _ptr(c), k, _ptr(out), int(reference), _stream_ptr(None))
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32).reshape(-1, 4)

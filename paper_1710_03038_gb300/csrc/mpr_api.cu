@@ -1,0 +1,1216 @@
+// C ABI of the MPR library: context, workspace layout, initialisation,
+// sweeps, temperature estimate, prediction and state access.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mpr_device.cuh"
+#include "mpr_internal.h"
+
+using namespace mpr;
+
+// ============================================================== errors
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mpr_status fail(mpr_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define MPR_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(MPR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define MPR_TRY(call)                      \
+    do {                                   \
+        mpr_status s_ = (call);            \
+        if (s_ != MPR_OK) return s_;       \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr double kPiD = 3.14159265358979323846;
+
+// ============================================================ layout
+
+// Byte offsets of the workspace regions of one context.
+struct Layout {
+    size_t img, ctl, ch_a, ch_cnt, ch_last, ch_ecur, ch_elast, ch_esum, ch_esum2;
+    size_t zst, gst, outst, eout, samp, slot_map, tiles, counts, halo, scratch;
+    size_t slot_pos, acc1, acc2, state, newton, sub;
+    size_t total;
+    long long n_slots;   // slot space over all images
+    long long n_state;   // floats of the state buffer
+};
+
+struct Geometry {
+    int n_img = 0, n_chains = 0, path = 0, tx = 64, ty = 64, halo_cap = 128;
+    std::vector<int> Lx, Ly;
+    std::vector<long long> site_off;
+    std::vector<int> tile0, ntiles;
+    long long n_sites = 0;
+    int n_tiles = 0;
+    int max_Lx = 0, max_Ly = 0;
+};
+
+void make_geometry(Geometry& g, int n_img, const int* Lx, const int* Ly, int n_chains, int path,
+                   int tx, int ty) {
+    g.n_img = n_img;
+    g.n_chains = n_chains;
+    g.path = path;
+    g.tx = tx;
+    g.ty = ty;
+    g.halo_cap = tx + ty;
+    g.Lx.assign(Lx, Lx + n_img);
+    g.Ly.assign(Ly, Ly + n_img);
+    g.site_off.resize(n_img);
+    g.tile0.resize(n_img);
+    g.ntiles.resize(n_img);
+    g.n_sites = 0;
+    g.n_tiles = 0;
+    g.max_Lx = g.max_Ly = 0;
+    for (int i = 0; i < n_img; ++i) {
+        g.site_off[i] = g.n_sites;
+        g.n_sites += (long long)Lx[i] * Ly[i];
+        const int nt = ((Lx[i] + tx - 1) / tx) * ((Ly[i] + ty - 1) / ty);
+        g.tile0[i] = g.n_tiles;
+        g.ntiles[i] = path == MPR_PATH_TILED ? nt : 0;
+        if (path == MPR_PATH_TILED) g.n_tiles += nt;
+        g.max_Lx = std::max(g.max_Lx, Lx[i]);
+        g.max_Ly = std::max(g.max_Ly, Ly[i]);
+    }
+}
+
+// Per image slot counts: tiled path = padded gap segments, plain = sites.
+Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_img,
+                   size_t sub_bytes, bool staging) {
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
+    const size_t NC = (size_t)g.n_img * g.n_chains;
+    const size_t N = (size_t)g.n_sites;
+    L.img = take(sizeof(ImgDev) * g.n_img);
+    L.ctl = take(sizeof(Control));
+    L.ch_a = take(sizeof(float) * NC);
+    L.ch_cnt = take(sizeof(uint32_t) * NC);
+    L.ch_last = take(sizeof(uint32_t) * NC);
+    L.ch_ecur = take(sizeof(double) * NC);
+    L.ch_elast = take(sizeof(double) * NC);
+    L.ch_esum = take(sizeof(double) * NC);
+    L.ch_esum2 = take(sizeof(double) * NC);
+    L.zst = take(staging ? sizeof(float) * N : 0);
+    L.gst = take(sizeof(uint8_t) * N);
+    L.outst = take(staging ? 2 * sizeof(float) * N : 0);
+    L.eout = take(sizeof(double) * NC);
+    L.samp = take(sizeof(float) * N);
+    const bool tiled = g.path == MPR_PATH_TILED;
+    L.slot_map = take(tiled ? sizeof(int) * N : 0);
+    L.tiles = take(sizeof(TileDesc) * g.n_tiles);
+    L.counts = take(sizeof(int) * 2 * g.n_tiles);
+    L.halo = take(sizeof(int2) * (size_t)g.n_tiles * 2 * g.halo_cap);
+    L.scratch = take(sizeof(double) * 4 * g.n_img);
+    L.n_slots = 0;
+    L.n_state = 0;
+    for (int i = 0; i < g.n_img; ++i) {
+        L.n_slots += slots_per_img[i];
+        L.n_state += slots_per_img[i] * g.n_chains;
+    }
+    L.slot_pos = take(tiled ? sizeof(uint32_t) * L.n_slots : 0);
+    L.acc1 = take(sizeof(double) * L.n_slots);
+    L.acc2 = take(sizeof(double) * L.n_slots);
+    L.state = take(sizeof(float) * L.n_state);
+    L.newton = take(sizeof(double) * 4 * g.n_img);
+    L.sub = take(sub_bytes);
+    L.total = o;
+    return L;
+}
+
+long long slot_bound(const Geometry& g, int i, long long n_gap) {
+    if (g.path != MPR_PATH_TILED) return (long long)g.Lx[i] * g.Ly[i];
+    return n_gap + 8LL * g.ntiles[i];
+}
+
+int default_T_side(int Lx, int Ly, const mpr_T_opts& o) {
+    if (o.L > 0) return o.L;
+    return std::min(256, std::max(Lx, Ly));
+}
+
+}  // namespace
+
+// ============================================================== context
+
+struct mpr_ctx {
+    mpr_params p{};
+    mpr_T_opts topt{};
+    Geometry g;
+    Layout L{};
+    unsigned char* ws = nullptr;
+    bool unconditional = false;   // the temperature lattices (no samples)
+    uint32_t img_tag = 0;
+    // device views
+    ImgDev* d_img = nullptr;
+    Control* d_ctl = nullptr;
+    ChainDev ch{};
+    float* d_samp = nullptr;
+    int* d_slot_map = nullptr;
+    TileDesc* d_tiles = nullptr;
+    int2* d_halo = nullptr;
+    uint32_t* d_slot_pos = nullptr;
+    double* d_acc1 = nullptr;
+    double* d_acc2 = nullptr;
+    float* d_state = nullptr;
+    float* d_zst = nullptr;
+    uint8_t* d_gst = nullptr;
+    float* d_out = nullptr;
+    double* d_eout = nullptr;
+    double* d_newton = nullptr;
+    // host mirrors
+    std::vector<ImgDev> h_img;
+    std::vector<long long> slots;
+    uint32_t sweep = 0, equil_index = 0;
+    long long n_meas_done = 0;
+    bool T_set = false;
+    mpr_ctx* sub = nullptr;   // unconditional lattices of the temperature estimate
+    ~mpr_ctx() { delete sub; }
+};
+
+namespace {
+
+template <typename T>
+T* at(unsigned char* base, size_t off) { return reinterpret_cast<T*>(base + off); }
+
+void bind_views(mpr_ctx* c) {
+    unsigned char* w = c->ws;
+    const Layout& L = c->L;
+    c->d_img = at<ImgDev>(w, L.img);
+    c->d_ctl = at<Control>(w, L.ctl);
+    c->ch.a = at<float>(w, L.ch_a);
+    c->ch.acc_cnt = at<uint32_t>(w, L.ch_cnt);
+    c->ch.acc_last = at<uint32_t>(w, L.ch_last);
+    c->ch.e_cur = at<double>(w, L.ch_ecur);
+    c->ch.e_last = at<double>(w, L.ch_elast);
+    c->ch.e_sum = at<double>(w, L.ch_esum);
+    c->ch.e_sum2 = at<double>(w, L.ch_esum2);
+    c->d_zst = at<float>(w, L.zst);
+    c->d_gst = at<uint8_t>(w, L.gst);
+    c->d_out = at<float>(w, L.outst);
+    c->d_eout = at<double>(w, L.eout);
+    c->d_samp = at<float>(w, L.samp);
+    c->d_slot_map = at<int>(w, L.slot_map);
+    c->d_tiles = at<TileDesc>(w, L.tiles);
+    c->d_halo = at<int2>(w, L.halo);
+    c->d_slot_pos = at<uint32_t>(w, L.slot_pos);
+    c->d_acc1 = at<double>(w, L.acc1);
+    c->d_acc2 = at<double>(w, L.acc2);
+    c->d_state = at<float>(w, L.state);
+    c->d_newton = at<double>(w, L.newton);
+}
+
+// ======================================================= init kernels
+
+__device__ __forceinline__ uint32_t ordered(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Extremes over sample sites and gap counts, per image (blockIdx.y).
+__global__ void minmax_kernel(const ImgDev* img, const float* z, const uint8_t* gap,
+                              uint32_t* mm, unsigned long long* ngap) {
+    const ImgDev& I = img[blockIdx.y];
+    const long long n = (long long)I.Lx * I.Ly;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    unsigned long long cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (gap[I.site_off + i]) { ++cnt; continue; }
+        const uint32_t o = ordered(z[I.site_off + i]);
+        lo = min(lo, o);
+        hi = max(hi, o);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mm + 2 * blockIdx.y, lo);
+        atomicMax(mm + 2 * blockIdx.y + 1, hi);
+        if (cnt) atomicAdd(ngap + blockIdx.y, cnt);
+    }
+}
+
+// Eq. map into the per-image sample plane (FP64 arithmetic, rounded once);
+// gap sites hold -1.
+__global__ void map_kernel(const ImgDev* img, const float* z, const uint8_t* gap, float* samp,
+                           int unconditional) {
+    const ImgDev& I = img[blockIdx.y];
+    const long long n = (long long)I.Lx * I.Ly;
+    const double zmin = I.zmin, scale = 2.0 * kPiD / ((double)I.zmax - (double)I.zmin);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = I.site_off + i;
+        samp[s] = (unconditional || gap[s]) ? -1.0f : (float)(((double)z[s] - zmin) * scale);
+    }
+}
+
+// Sample specific energy (Eq. mpr-sse) sums: -J sum cos(q dphi) over sample
+// pairs (right and down bonds), FP64.
+__global__ void sample_energy_kernel(const ImgDev* img, const float* samp, double q, double J,
+                                     double* sums, unsigned long long* npairs) {
+    const ImgDev& I = img[blockIdx.y];
+    const long long n = (long long)I.Lx * I.Ly;
+    double s = 0.0;
+    unsigned long long cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = samp[I.site_off + i];
+        if (v < 0.0f) continue;
+        const int x = (int)(i % I.Lx), y = (int)(i / I.Lx);
+        if (x + 1 < I.Lx) {
+            const float w = samp[I.site_off + i + 1];
+            if (w >= 0.0f) { s -= J * cos(q * ((double)v - (double)w)); ++cnt; }
+        }
+        if (y + 1 < I.Ly) {
+            const float w = samp[I.site_off + i + I.Lx];
+            if (w >= 0.0f) { s -= J * cos(q * ((double)v - (double)w)); ++cnt; }
+        }
+    }
+    s = warp_sum(s);
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((threadIdx.x & 31) == 0) {
+        if (s != 0.0) atomicAdd(sums + blockIdx.y, s);
+        if (cnt) atomicAdd(npairs + blockIdx.y, cnt);
+    }
+}
+
+// Hot start of the tiled state: slot -> 2 pi u with the site's first uniform
+// at sweep 0xFFFFFFFF; padding slots hold 0.
+__global__ void hot_start_tiled_kernel(const ImgDev* img, const uint32_t* slot_pos, float* state,
+                                       long long slots_img, int img_i, int n_chains, uint2 key,
+                                       uint32_t img_tag) {
+    const ImgDev& I = img[img_i];
+    const long long total = slots_img * n_chains;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int chain = (int)(t / slots_img);
+        const long long k = t - (long long)chain * slots_img;
+        const uint32_t p = slot_pos[I.slot_off + k];
+        float v = 0.0f;
+        if (p != 0xFFFFFFFFu) {
+            const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
+            uint32_t wu, wr;
+            site_uniform_words(X, Y, (X + Y) & 1, 0xFFFFFFFFu, (uint32_t)chain,
+                               (uint32_t)img_i | img_tag, key, wu, wr);
+            v = kTwoPi * u24(wu);
+        }
+        state[I.state_off + (long long)chain * I.stride + k] = v;
+    }
+}
+
+// Dense planes of the plain path: fixed angle with the sign bit at samples,
+// hot start at gaps.
+__global__ void init_plain_kernel(const ImgDev* img, const float* samp, float* state,
+                                  int img_i, int n_chains, uint2 key, uint32_t img_tag) {
+    const ImgDev& I = img[img_i];
+    const long long n = (long long)I.Lx * I.Ly;
+    const long long total = n * n_chains;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int chain = (int)(t / n);
+        const long long i = t - (long long)chain * n;
+        const float v = samp[I.site_off + i];
+        float out;
+        if (v >= 0.0f) {
+            out = as_fixed(v);
+        } else {
+            const int X = (int)(i % I.Lx), Y = (int)(i / I.Lx);
+            uint32_t wu, wr;
+            site_uniform_words(X, Y, (X + Y) & 1, 0xFFFFFFFFu, (uint32_t)chain,
+                               (uint32_t)img_i | img_tag, key, wu, wr);
+            out = kTwoPi * u24(wu);
+        }
+        state[I.state_off + (long long)chain * I.stride + i] = out;
+    }
+}
+
+__global__ void init_chains_kernel(ChainDev ch, int nc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        ch.a[i] = 1.0f;
+        ch.acc_cnt[i] = 0;
+        ch.acc_last[i] = 0;
+        ch.e_cur[i] = 0.0;
+        ch.e_last[i] = __longlong_as_double(0x7FF8000000000000LL);
+        ch.e_sum[i] = 0.0;
+        ch.e_sum2[i] = 0.0;
+    }
+}
+
+// ======================================================= sweep kernels
+
+// Bookkeeping after every sweep: acceptance -> a (Alg. 2 step 4.2), energy
+// record (step 4.3), counters.  One block.
+__global__ void end_sweep_kernel(const ImgDev* img, ChainDev ch, Control* ctl, int n_img,
+                                 int n_chains, int equil, int record, int stats, int add_ess,
+                                 double A_targ, double k_a) {
+    const uint32_t i = ctl->equil_index;
+    const int nc = n_img * n_chains;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const ImgDev& I = img[c / n_chains];
+        const uint32_t cnt = ch.acc_cnt[c];
+        ch.acc_last[c] = cnt;
+        ch.acc_cnt[c] = 0;
+        if (equil && (double)cnt < A_targ * (double)I.n_gap)
+            ch.a[c] = (float)(1.0 + (double)(i + 1) / k_a);
+        if (record) {
+            const double e = (ch.e_cur[c] + (add_ess ? I.E_ss : 0.0)) / I.n_bonds;
+            ch.e_last[c] = e;
+            ch.e_cur[c] = 0.0;
+            if (stats) {
+                ch.e_sum[c] += e;
+                ch.e_sum2[c] += e * e;
+            }
+        } else {
+            ch.e_last[c] = __longlong_as_double(0x7FF8000000000000LL);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->sweep += 1;
+        if (equil) ctl->equil_index += 1;
+    }
+}
+
+// One Newton step of the specific energy matching per image (thread):
+// <e>, Var(e) over the chains' measurement sweeps, bracket update, then
+// T <- T - (<e> - e_s) T^2 / (N_GP Var(e)), or the geometric bisection of the
+// bracket when the step leaves it.
+__global__ void newton_kernel(ImgDev* sub_img, ImgDev* main_img, ChainDev sub_ch, double* nst,
+                              int n_img, int K, int n_meas) {
+    const int im = blockIdx.x * blockDim.x + threadIdx.x;
+    if (im >= n_img) return;
+    double s = 0.0, s2 = 0.0;
+    for (int k = 0; k < K; ++k) {
+        s += sub_ch.e_sum[im * K + k];
+        s2 += sub_ch.e_sum2[im * K + k];
+        sub_ch.e_sum[im * K + k] = 0.0;
+        sub_ch.e_sum2[im * K + k] = 0.0;
+    }
+    const double n = (double)K * n_meas;
+    const double mean = s / n;
+    const double var = fmax(s2 / n - mean * mean, 1e-300);
+    double* st = nst + 4 * im;
+    double lo = st[0], hi = st[1];
+    const double T = st[2];
+    const double e_s = main_img[im].e_s;
+    if (mean > e_s) hi = fmin(hi, T); else lo = fmax(lo, T);
+    const double slope = sub_img[im].n_bonds * var / (T * T);
+    double Tn = T - (mean - e_s) / slope;
+    if (!(Tn > lo && Tn < hi)) Tn = sqrt(lo * hi);
+    st[0] = lo;
+    st[1] = hi;
+    st[2] = Tn;
+    st[3] = mean;
+    sub_img[im].T = Tn;
+    sub_img[im].invT = (float)(1.0 / Tn);
+    main_img[im].T = Tn;
+    main_img[im].invT = (float)(1.0 / Tn);
+}
+
+__global__ void newton_init_kernel(ImgDev* sub_img, const ImgDev* main_img, double* nst,
+                                   int n_img, double T_lo, double T_hi, double J) {
+    const int im = blockIdx.x * blockDim.x + threadIdx.x;
+    if (im >= n_img) return;
+    // harmonic guess e ~ -J + T/4 (each site carries T/2 over two bonds)
+    double T0 = 4.0 * (main_img[im].e_s + J);
+    T0 = fmin(fmax(T0, T_lo * 4.0), T_hi / 4.0);
+    nst[4 * im + 0] = T_lo;
+    nst[4 * im + 1] = T_hi;
+    nst[4 * im + 2] = T0;
+    nst[4 * im + 3] = 0.0;
+    sub_img[im].T = T0;
+    sub_img[im].invT = (float)(1.0 / T0);
+}
+
+// ======================================================= dense views
+
+__device__ __forceinline__ float site_value(const ImgDev& I, const float* state, const float* samp,
+                                            const int* slot_map, int tiled, int chain,
+                                            long long i) {
+    const float* st = state + I.state_off + (long long)chain * I.stride;
+    if (tiled) {
+        const int s = slot_map[I.site_off + i];
+        return s >= 0 ? st[s] : samp[I.site_off + i];
+    }
+    return fabsf(st[i]);
+}
+
+// H of every (image, chain) (blockIdx.y), FP64 sums of FP32 bond terms.
+__global__ void energy_kernel(const ImgDev* img, const float* state, const float* samp,
+                              const int* slot_map, int tiled, int n_chains, float q, float J,
+                              double* out) {
+    const int ic = blockIdx.y;
+    const int im = ic / n_chains, chain = ic - im * n_chains;
+    const ImgDev& I = img[im];
+    const long long n = (long long)I.Lx * I.Ly;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % I.Lx), y = (int)(i / I.Lx);
+        const float v = site_value(I, state, samp, slot_map, tiled, chain, i);
+        float e = 0.0f;
+        if (x + 1 < I.Lx)
+            e -= J * cosf(q * (v - site_value(I, state, samp, slot_map, tiled, chain, i + 1)));
+        if (y + 1 < I.Ly)
+            e -= J * cosf(q * (v - site_value(I, state, samp, slot_map, tiled, chain, i + I.Lx)));
+        s += (double)e;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out + ic, s);
+}
+
+__global__ void energy_finish_kernel(const ImgDev* img, double* out, int n_chains, int nc) {
+    const int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic < nc) out[ic] /= img[ic / n_chains].n_bonds;
+}
+
+// state <-> dense [chain][Ly][Lx] per image (dir 0: get, 1: set gap sites).
+__global__ void state_copy_kernel(const ImgDev* img, float* state, const float* samp,
+                                  const int* slot_map, int tiled, int n_chains, float* dense,
+                                  int dir, int ic0, float* plane) {
+    const int ic = ic0 + blockIdx.y;
+    const int im = ic / n_chains, chain = ic - im * n_chains;
+    const ImgDev& I = img[im];
+    const long long n = (long long)I.Lx * I.Ly;
+    float* d = plane ? plane : dense + I.site_off * n_chains + (long long)chain * n;
+    float* st = state + I.state_off + (long long)chain * I.stride;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (tiled) {
+            const int s = slot_map[I.site_off + i];
+            if (dir == 0) d[i] = s >= 0 ? st[s] : samp[I.site_off + i];
+            else if (s >= 0) st[s] = d[i];
+        } else {
+            const float v = st[i];
+            if (dir == 0) d[i] = fabsf(v);
+            else if (!is_fixed(v)) st[i] = d[i];
+        }
+    }
+}
+
+// Conditional mean and standard deviation over realisations (Alg. 2 step 6).
+__global__ void predict_kernel(const ImgDev* img, const double* acc1, const double* acc2,
+                               const float* zin, const int* slot_map, const float* samp,
+                               int tiled, double n_samples, float* zhat, float* zstd) {
+    const ImgDev& I = img[blockIdx.y];
+    const long long n = (long long)I.Lx * I.Ly;
+    const double range = (double)I.zmax - (double)I.zmin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = I.site_off + i;
+        long long slot = -1;
+        if (tiled) slot = slot_map[s];
+        else if (samp[s] < 0.0f) slot = i;
+        if (slot < 0) {
+            zhat[s] = zin[s];
+            if (zstd) zstd[s] = 0.0f;
+        } else {
+            const double m = acc1[I.slot_off + slot] / n_samples;
+            zhat[s] = (float)(I.zmin + range * m / (2.0 * kPiD));
+            if (zstd) {
+                const double v = fmax(acc2[I.slot_off + slot] / n_samples - m * m, 0.0);
+                zstd[s] = (float)(range * sqrt(v) / (2.0 * kPiD));
+            }
+        }
+    }
+}
+
+__global__ void set_T_kernel(ImgDev* img, const double* T, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { img[i].T = T[i]; img[i].invT = (float)(1.0 / T[i]); }
+}
+
+int grid_for(long long n, int block = 256, int cap = 4096) {
+    long long b = (n + block - 1) / block;
+    return (int)std::max<long long>(1, std::min<long long>(b, cap));
+}
+
+// ======================================================= host helpers
+
+mpr_status check_params(const mpr_params* p) {
+    if (!p) return fail(MPR_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->q > 0.0 && p->q <= 0.5 + 1e-12) && !(p->q == 1.0))
+        return fail(MPR_ERR_INVALID_ARG, "q must lie in (0, 1/2] (or equal 1)");
+    if (!(p->J > 0.0)) return fail(MPR_ERR_INVALID_ARG, "J must be positive");
+    if (!(p->A_targ >= 0.0 && p->A_targ <= 1.0)) return fail(MPR_ERR_INVALID_ARG, "A_targ in [0,1]");
+    if (!(p->k_a > 0.0)) return fail(MPR_ERR_INVALID_ARG, "k_a must be positive");
+    if (p->path != MPR_PATH_TILED && p->path != MPR_PATH_PLAIN)
+        return fail(MPR_ERR_INVALID_ARG, "unknown path");
+    if (p->chain_group < 0) return fail(MPR_ERR_INVALID_ARG, "chain_group < 0");
+    return MPR_OK;
+}
+
+void pick_tiles(const mpr_params& p, int n_img, const int* Lx, const int* Ly, int n_chains,
+                int& tx, int& ty) {
+    tx = p.tile_x;
+    ty = p.tile_y;
+    if (tx > 0 && ty > 0) return;
+    long long n = 0;
+    int mx = 0;
+    for (int i = 0; i < n_img; ++i) { n += (long long)Lx[i] * Ly[i]; mx = std::max(mx, std::max(Lx[i], Ly[i])); }
+    (void)n_chains;
+    if (mx <= 48) { tx = 32; ty = 16; }
+    else if (mx <= 96) { tx = 32; ty = 32; }
+    else { tx = 64; ty = 64; }
+}
+
+int pick_chain_group(const mpr_ctx* c) {
+    if (c->p.chain_group > 0) return std::min(c->p.chain_group, 64);
+    if (c->g.path != MPR_PATH_TILED) return 1;
+    // enough thread blocks to fill the GPU several times over
+    const long long target = 152LL * 8;
+    const long long tiles = std::max(1, c->g.n_tiles);
+    int cg = (int)std::min<long long>(64, std::max<long long>(1, tiles * c->g.n_chains / target));
+    cg = std::min(cg, c->g.n_chains);
+    return std::max(cg, 1);
+}
+
+mpr_status sub_workspace_size(const mpr_params& p, const mpr_T_opts& o, int n_img, const int* Lx,
+                              const int* Ly, size_t* bytes);
+
+mpr_status workspace_size_impl(int n_img, const int* Lx, const int* Ly, const int64_t* n_gap,
+                               int n_chains, const mpr_params& p, const mpr_T_opts& o,
+                               bool with_sub, bool staging, size_t* bytes) {
+    int tx, ty;
+    pick_tiles(p, n_img, Lx, Ly, n_chains, tx, ty);
+    if (p.path == MPR_PATH_TILED && !tiled_config_supported(tx, ty))
+        return fail(MPR_ERR_INVALID_ARG, "unsupported tile shape");
+    Geometry g;
+    make_geometry(g, n_img, Lx, Ly, n_chains, p.path, tx, ty);
+    std::vector<long long> slots(n_img);
+    for (int i = 0; i < n_img; ++i)
+        slots[i] = slot_bound(g, i, n_gap ? (long long)n_gap[i] : (long long)Lx[i] * Ly[i]);
+    size_t sub = 0;
+    if (with_sub) MPR_TRY(sub_workspace_size(p, o, n_img, Lx, Ly, &sub));
+    *bytes = make_layout(g, slots, sub, staging).total;
+    return MPR_OK;
+}
+
+mpr_status sub_workspace_size(const mpr_params& p, const mpr_T_opts& o, int n_img, const int* Lx,
+                              const int* Ly, size_t* bytes) {
+    std::vector<int> L(n_img);
+    for (int i = 0; i < n_img; ++i) L[i] = default_T_side(Lx[i], Ly[i], o);
+    mpr_params sp = p;
+    sp.path = MPR_PATH_TILED;
+    sp.tile_x = sp.tile_y = 0;
+    sp.chain_group = 0;
+    return workspace_size_impl(n_img, L.data(), L.data(), nullptr, o.chains, sp, o, false, false,
+                               bytes);
+}
+
+mpr_status validate_shapes(int n_img, const int* Lx, const int* Ly, int n_chains) {
+    if (n_img < 1 || !Lx || !Ly) return fail(MPR_ERR_INVALID_ARG, "need n_img >= 1 and sizes");
+    if (n_chains < 1 || n_chains > 65535) return fail(MPR_ERR_INVALID_ARG, "n_chains out of range");
+    if ((long long)n_img * n_chains > 65535)
+        return fail(MPR_ERR_INVALID_ARG, "n_img * n_chains must not exceed 65535");
+    for (int i = 0; i < n_img; ++i)
+        if (Lx[i] < 2 || Ly[i] < 2 || Lx[i] > 65535 || Ly[i] > 65535)
+            return fail(MPR_ERR_INVALID_ARG, "image sides must lie in [2, 65535]");
+    return MPR_OK;
+}
+
+// Builds a context over `ws`.  unconditional: every site free, no inputs.
+mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_chains,
+                     const float* z, const uint8_t* gap, mpr_mem where, void* ws, size_t ws_bytes,
+                     bool unconditional, cudaStream_t s) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+        return fail(MPR_ERR_WORKSPACE, "workspace must be non-NULL and 256-byte aligned");
+    int tx, ty;
+    pick_tiles(c->p, n_img, Lx, Ly, n_chains, tx, ty);
+    if (c->p.path == MPR_PATH_TILED && !tiled_config_supported(tx, ty))
+        return fail(MPR_ERR_INVALID_ARG, "unsupported tile shape");
+    c->unconditional = unconditional;
+    c->img_tag = unconditional ? (1u << 30) : 0u;
+    make_geometry(c->g, n_img, Lx, Ly, n_chains, c->p.path, tx, ty);
+    Geometry& g = c->g;
+    const bool tiled = g.path == MPR_PATH_TILED;
+    const bool staging = !unconditional;
+    size_t sub_bytes = 0;
+    if (!unconditional) MPR_TRY(sub_workspace_size(c->p, c->topt, n_img, Lx, Ly, &sub_bytes));
+
+    // provisional layout (worst case) to place the regions that do not depend on gap counts
+    std::vector<long long> worst(n_img);
+    for (int i = 0; i < n_img; ++i) worst[i] = 0;
+    c->ws = static_cast<unsigned char*>(ws);
+    c->L = make_layout(g, worst, 0, staging);
+    if (c->L.scratch + align_up(sizeof(double) * 4 * n_img) > ws_bytes)
+        return fail(MPR_ERR_WORKSPACE, "workspace too small");
+    bind_views(c);
+
+    c->h_img.assign(n_img, ImgDev{});
+    for (int i = 0; i < n_img; ++i) {
+        ImgDev& I = c->h_img[i];
+        I.Lx = Lx[i];
+        I.Ly = Ly[i];
+        I.site_off = g.site_off[i];
+        I.tile0 = g.tile0[i];
+        I.ntiles = g.ntiles[i];
+        I.n_bonds = (double)Lx[i] * (Ly[i] - 1) + (double)Ly[i] * (Lx[i] - 1);
+        I.T = 1.0;
+        I.invT = 1.0f;
+    }
+    MPR_CUDA(cudaMemcpyAsync(c->d_img, c->h_img.data(), sizeof(ImgDev) * n_img,
+                             cudaMemcpyHostToDevice, s));
+    const size_t N = (size_t)g.n_sites;
+    const float* d_z = nullptr;
+    const uint8_t* d_gap = c->d_gst;
+    if (unconditional) {
+        MPR_CUDA(cudaMemsetAsync(c->d_gst, 1, N, s));
+    } else {
+        const cudaMemcpyKind k = where == MPR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        MPR_CUDA(cudaMemcpyAsync(c->d_zst, z, sizeof(float) * N, k, s));
+        MPR_CUDA(cudaMemcpyAsync(c->d_gst, gap, N, k, s));
+        d_z = c->d_zst;
+    }
+
+    // tile descriptors
+    std::vector<TileDesc> tiles;
+    if (tiled) {
+        tiles.reserve(g.n_tiles);
+        for (int i = 0; i < n_img; ++i)
+            for (int y0 = 0; y0 < Ly[i]; y0 += ty)
+                for (int x0 = 0; x0 < Lx[i]; x0 += tx) {
+                    TileDesc t{};
+                    t.img = i;
+                    t.x0 = x0;
+                    t.y0 = y0;
+                    tiles.push_back(t);
+                }
+        MPR_CUDA(cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(TileDesc) * g.n_tiles,
+                                 cudaMemcpyHostToDevice, s));
+    }
+
+    // extremes and gap counts
+    double* scratch = at<double>(c->ws, c->L.scratch);
+    uint32_t* mm = reinterpret_cast<uint32_t*>(scratch);                         // [2 n_img]
+    unsigned long long* ngap = reinterpret_cast<unsigned long long*>(scratch + n_img);  // [n_img]
+    std::vector<uint32_t> h_mm(2 * n_img);
+    for (int i = 0; i < n_img; ++i) { h_mm[2 * i] = 0xFFFFFFFFu; h_mm[2 * i + 1] = 0u; }
+    MPR_CUDA(cudaMemcpyAsync(mm, h_mm.data(), sizeof(uint32_t) * 2 * n_img, cudaMemcpyHostToDevice, s));
+    MPR_CUDA(cudaMemsetAsync(ngap, 0, sizeof(unsigned long long) * n_img, s));
+    std::vector<unsigned long long> h_ngap(n_img, 0);
+    if (!unconditional) {
+        long long maxn = 0;
+        for (int i = 0; i < n_img; ++i) maxn = std::max(maxn, (long long)Lx[i] * Ly[i]);
+        minmax_kernel<<<dim3(grid_for(maxn, 256, 1024), n_img), 256, 0, s>>>(c->d_img, d_z, d_gap, mm, ngap);
+        MPR_CUDA(cudaGetLastError());
+    }
+    std::vector<int> h_counts;
+    if (tiled) {
+        int* counts = at<int>(c->ws, c->L.counts);
+        MPR_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * 2 * g.n_tiles, s));
+        MPR_CUDA(launch_tile_count(c->d_img, c->d_tiles, g.n_tiles, d_gap, tx, ty, counts, s));
+        h_counts.resize(2 * g.n_tiles);
+        MPR_CUDA(cudaMemcpyAsync(h_counts.data(), counts, sizeof(int) * 2 * g.n_tiles,
+                                 cudaMemcpyDeviceToHost, s));
+    }
+    if (!unconditional) {
+        MPR_CUDA(cudaMemcpyAsync(h_mm.data(), mm, sizeof(uint32_t) * 2 * n_img, cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaMemcpyAsync(h_ngap.data(), ngap, sizeof(unsigned long long) * n_img,
+                                 cudaMemcpyDeviceToHost, s));
+    }
+    MPR_CUDA(cudaStreamSynchronize(s));
+
+    // per image: range, gap count, slot space
+    c->slots.assign(n_img, 0);
+    for (int i = 0; i < n_img; ++i) {
+        ImgDev& I = c->h_img[i];
+        if (unconditional) {
+            I.zmin = 0.0f;
+            I.zmax = 1.0f;
+            I.n_gap = (long long)Lx[i] * Ly[i];
+        } else {
+            auto dec = [](uint32_t u) {
+                uint32_t b = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+                float f;
+                std::memcpy(&f, &b, 4);
+                return f;
+            };
+            if (h_mm[2 * i] == 0xFFFFFFFFu)
+                return fail(MPR_ERR_DEGENERATE_RANGE, "image " + std::to_string(i) + " has no samples");
+            I.zmin = dec(h_mm[2 * i]);
+            I.zmax = dec(h_mm[2 * i + 1]);
+            if (!(I.zmax > I.zmin))
+                return fail(MPR_ERR_DEGENERATE_RANGE,
+                            "image " + std::to_string(i) + ": z_max == z_min over the samples");
+            if (!std::isfinite(I.zmin) || !std::isfinite(I.zmax))
+                return fail(MPR_ERR_INVALID_ARG, "non-finite sample value in image " + std::to_string(i));
+            I.n_gap = (long long)h_ngap[i];
+            if (I.n_gap == 0)
+                return fail(MPR_ERR_INVALID_ARG, "image " + std::to_string(i) + " has no gaps");
+        }
+        if (tiled) {
+            long long off = 0;
+            for (int t = g.tile0[i]; t < g.tile0[i] + g.ntiles[i]; ++t) {
+                for (int col = 0; col < 2; ++col) {
+                    const int n = h_counts[2 * t + col];
+                    tiles[t].off[col] = (int)off;
+                    tiles[t].cnt[col] = n;
+                    off += (n + 3) & ~3;
+                }
+            }
+            c->slots[i] = off;
+        } else {
+            c->slots[i] = (long long)Lx[i] * Ly[i];
+        }
+    }
+    c->L = make_layout(g, c->slots, sub_bytes, staging);
+    if (c->L.total > ws_bytes)
+        return fail(MPR_ERR_WORKSPACE, "workspace too small: need " + std::to_string(c->L.total) +
+                                           " bytes, have " + std::to_string(ws_bytes));
+    bind_views(c);
+    long long slot_off = 0, state_off = 0;
+    for (int i = 0; i < n_img; ++i) {
+        ImgDev& I = c->h_img[i];
+        I.slot_off = slot_off;
+        I.state_off = state_off;
+        I.stride = c->slots[i];
+        slot_off += c->slots[i];
+        state_off += c->slots[i] * n_chains;
+    }
+    MPR_CUDA(cudaMemcpyAsync(c->d_img, c->h_img.data(), sizeof(ImgDev) * n_img,
+                             cudaMemcpyHostToDevice, s));
+    if (tiled) {
+        MPR_CUDA(cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(TileDesc) * g.n_tiles,
+                                 cudaMemcpyHostToDevice, s));
+        MPR_CUDA(cudaMemsetAsync(c->d_slot_pos, 0xFF, sizeof(uint32_t) * c->L.n_slots, s));
+        MPR_CUDA(launch_tile_fill(c->d_img, c->d_tiles, g.n_tiles, d_gap, tx, ty, c->d_slot_pos,
+                                  c->d_slot_map, c->d_halo, g.halo_cap, s));
+    }
+    long long maxn = 0;
+    for (int i = 0; i < n_img; ++i) maxn = std::max(maxn, (long long)Lx[i] * Ly[i]);
+    map_kernel<<<dim3(grid_for(maxn, 256, 2048), n_img), 256, 0, s>>>(c->d_img, d_z, d_gap, c->d_samp,
+                                                                      unconditional ? 1 : 0);
+    MPR_CUDA(cudaGetLastError());
+    const uint2 key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
+    for (int i = 0; i < n_img; ++i) {
+        if (tiled) {
+            hot_start_tiled_kernel<<<grid_for(c->slots[i] * n_chains), 256, 0, s>>>(
+                c->d_img, c->d_slot_pos, c->d_state, c->slots[i], i, n_chains, key, c->img_tag);
+        } else {
+            init_plain_kernel<<<grid_for((long long)Lx[i] * Ly[i] * n_chains), 256, 0, s>>>(
+                c->d_img, c->d_samp, c->d_state, i, n_chains, key, c->img_tag);
+        }
+        MPR_CUDA(cudaGetLastError());
+    }
+    const int nc = n_img * n_chains;
+    init_chains_kernel<<<grid_for(nc), 256, 0, s>>>(c->ch, nc);
+    MPR_CUDA(cudaGetLastError());
+    MPR_CUDA(cudaMemsetAsync(c->d_ctl, 0, sizeof(Control), s));
+    MPR_CUDA(cudaMemsetAsync(c->d_acc1, 0, sizeof(double) * c->L.n_slots, s));
+    MPR_CUDA(cudaMemsetAsync(c->d_acc2, 0, sizeof(double) * c->L.n_slots, s));
+
+    // sample specific energy
+    if (!unconditional) {
+        double* sums = scratch + 2 * n_img;
+        unsigned long long* npairs = reinterpret_cast<unsigned long long*>(scratch + 3 * n_img);
+        MPR_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 2 * n_img, s));
+        sample_energy_kernel<<<dim3(grid_for(maxn, 256, 1024), n_img), 256, 0, s>>>(
+            c->d_img, c->d_samp, c->p.q, c->p.J, sums, npairs);
+        MPR_CUDA(cudaGetLastError());
+        std::vector<double> h_sums(n_img);
+        std::vector<unsigned long long> h_np(n_img);
+        MPR_CUDA(cudaMemcpyAsync(h_sums.data(), sums, sizeof(double) * n_img, cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaMemcpyAsync(h_np.data(), npairs, sizeof(unsigned long long) * n_img,
+                                 cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n_img; ++i) {
+            ImgDev& I = c->h_img[i];
+            I.n_sp = (long long)h_np[i];
+            I.E_ss = h_sums[i];
+            I.e_s = I.n_sp > 0 ? h_sums[i] / (double)I.n_sp : std::nan("");
+        }
+        MPR_CUDA(cudaMemcpyAsync(c->d_img, c->h_img.data(), sizeof(ImgDev) * n_img,
+                                 cudaMemcpyHostToDevice, s));
+    }
+    c->sweep = 0;
+    c->equil_index = 0;
+    c->n_meas_done = 0;
+    return MPR_OK;
+}
+
+mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool accumulate,
+                      cudaStream_t s) {
+    const bool equil = phase == MPR_EQUIL;
+    const bool record = (flags & MPR_RECORD_ENERGY) != 0;
+    SweepArgs a{};
+    a.img = c->d_img;
+    a.tiles = c->d_tiles;
+    a.slot_pos = c->d_slot_pos;
+    a.halo = c->d_halo;
+    a.samp = c->d_samp;
+    a.state = c->d_state;
+    a.acc1 = c->d_acc1;
+    a.acc2 = c->d_acc2;
+    a.ch = c->ch;
+    a.ctl = c->d_ctl;
+    a.key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
+    a.q = (float)c->p.q;
+    a.inv_q = (float)(1.0 / c->p.q);
+    a.two_pi_q = (float)(2.0 * kPiD * c->p.q);
+    a.J = (float)c->p.J;
+    a.n_chains = c->g.n_chains;
+    a.chain_group = pick_chain_group(c);
+    a.halo_cap = c->g.halo_cap;
+    a.n_img = c->g.n_img;
+    a.img_tag = c->img_tag;
+    int base = 0;
+    if (!equil && accumulate) base |= kAccumulate | kAccumulate2;
+    if (!equil && !c->p.freeze_a_in_measure) base |= kAlphaOne;
+    const bool tiled = c->g.path == MPR_PATH_TILED;
+    for (int k = 0; k < n; ++k) {
+        for (int colour = 0; colour < 2; ++colour) {
+            a.colour = colour;
+            a.flags = base | ((record && colour == 1) ? kEnergy : 0);
+            cudaError_t e = tiled ? launch_tiled_pass(a, c->g.n_tiles, c->g.tx, c->g.ty, s)
+                                  : launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
+            if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
+        }
+        end_sweep_kernel<<<1, 256, 0, s>>>(c->d_img, c->ch, c->d_ctl, c->g.n_img, c->g.n_chains,
+                                           equil ? 1 : 0, record ? 1 : 0, stats ? 1 : 0,
+                                           tiled ? 1 : 0, c->p.A_targ, c->p.k_a);
+        MPR_CUDA(cudaGetLastError());
+    }
+    c->sweep += (uint32_t)n;
+    if (equil) c->equil_index += (uint32_t)n;
+    if (!equil && accumulate) c->n_meas_done += n;
+    return MPR_OK;
+}
+
+}  // namespace
+
+// ================================================================= ABI
+
+extern "C" {
+
+const char* mpr_version(void) { return "mpr-gb300 0.1 (sm_103a)"; }
+const char* mpr_last_error(void) { return g_last_error.c_str(); }
+
+const char* mpr_status_string(mpr_status s) {
+    switch (s) {
+        case MPR_OK: return "ok";
+        case MPR_ERR_INVALID_ARG: return "invalid argument";
+        case MPR_ERR_CUDA: return "CUDA error";
+        case MPR_ERR_DEGENERATE_RANGE: return "degenerate sample range";
+        case MPR_ERR_NO_SAMPLE_PAIRS: return "no sample pairs";
+        case MPR_ERR_T_OUT_OF_RANGE: return "temperature out of range";
+        case MPR_ERR_WORKSPACE: return "workspace error";
+        case MPR_ERR_STATE: return "invalid state";
+        case MPR_ERR_DEVICE: return "device-side error";
+        default: return "unknown status";
+    }
+}
+
+mpr_status mpr_default_params(mpr_params* p) {
+    if (!p) return fail(MPR_ERR_INVALID_ARG, "NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->q = 0.5;
+    p->J = 1.0;
+    p->A_targ = 0.3;
+    p->k_a = 3.0;
+    p->seed = 0x2545F4914F6CDD1DULL;
+    p->freeze_a_in_measure = 1;
+    p->path = MPR_PATH_TILED;
+    return MPR_OK;
+}
+
+mpr_status mpr_default_T_opts(mpr_T_opts* o) {
+    if (!o) return fail(MPR_ERR_INVALID_ARG, "NULL");
+    o->L = 0;
+    o->chains = 4;
+    o->n_equil = 60;
+    o->n_meas = 120;
+    o->iters = 6;
+    o->T_lo = 1e-5;
+    o->T_hi = 20.0;
+    return MPR_OK;
+}
+
+mpr_status mpr_workspace_size(int n_img, const int* Lx, const int* Ly, const int64_t* n_gap,
+                              int n_chains, const mpr_params* p, const mpr_T_opts* T_opts,
+                              size_t* bytes) {
+    if (!bytes) return fail(MPR_ERR_INVALID_ARG, "bytes is NULL");
+    MPR_TRY(validate_shapes(n_img, Lx, Ly, n_chains));
+    MPR_TRY(check_params(p));
+    mpr_T_opts o;
+    mpr_default_T_opts(&o);
+    if (T_opts) o = *T_opts;
+    if (o.chains < 1) return fail(MPR_ERR_INVALID_ARG, "T_opts.chains < 1");
+    return workspace_size_impl(n_img, Lx, Ly, n_gap, n_chains, *p, o, true, true, bytes);
+}
+
+mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly, int n_chains,
+                         const mpr_params* p, const mpr_T_opts* T_opts, const float* z,
+                         const uint8_t* gap, mpr_mem where, void* workspace, size_t ws_bytes,
+                         mpr_stream stream) {
+    if (!out) return fail(MPR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    MPR_TRY(validate_shapes(n_img, Lx, Ly, n_chains));
+    MPR_TRY(check_params(p));
+    if (!z || !gap) return fail(MPR_ERR_INVALID_ARG, "z and gap are required");
+    if (where != MPR_HOST && where != MPR_DEVICE) return fail(MPR_ERR_INVALID_ARG, "bad mpr_mem");
+    mpr_ctx* c = new (std::nothrow) mpr_ctx();
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "out of host memory");
+    c->p = *p;
+    mpr_default_T_opts(&c->topt);
+    if (T_opts) c->topt = *T_opts;
+    if (c->topt.chains < 1 || c->topt.n_meas < 1 || c->topt.iters < 0 || c->topt.n_equil < 0 ||
+        !(c->topt.T_lo > 0.0 && c->topt.T_hi > c->topt.T_lo)) {
+        delete c;
+        return fail(MPR_ERR_INVALID_ARG, "bad temperature-estimate options");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    mpr_status st = init_impl(c, n_img, Lx, Ly, n_chains, z, gap, where, workspace, ws_bytes, false, s);
+    if (st != MPR_OK) { delete c; return st; }
+    // unconditional lattices of the temperature estimate
+    c->sub = new (std::nothrow) mpr_ctx();
+    if (!c->sub) { delete c; return fail(MPR_ERR_INVALID_ARG, "out of host memory"); }
+    c->sub->p = c->p;
+    c->sub->p.path = MPR_PATH_TILED;
+    c->sub->p.tile_x = c->sub->p.tile_y = 0;
+    c->sub->p.chain_group = 0;
+    c->sub->topt = c->topt;
+    std::vector<int> LT(n_img);
+    for (int i = 0; i < n_img; ++i) LT[i] = default_T_side(Lx[i], Ly[i], c->topt);
+    size_t sub_bytes;
+    st = sub_workspace_size(c->p, c->topt, n_img, Lx, Ly, &sub_bytes);
+    if (st == MPR_OK)
+        st = init_impl(c->sub, n_img, LT.data(), LT.data(), c->topt.chains, nullptr, nullptr,
+                       MPR_DEVICE, c->ws + c->L.sub, sub_bytes, true, s);
+    if (st == MPR_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail(MPR_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (st != MPR_OK) { delete c; return st; }
+    *out = c;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_image_info(const mpr_ctx* c, double* e_s, int64_t* n_sp, int64_t* n_gap,
+                              float* z_min, float* z_max) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    for (int i = 0; i < c->g.n_img; ++i) {
+        const ImgDev& I = c->h_img[i];
+        if (e_s) e_s[i] = I.e_s;
+        if (n_sp) n_sp[i] = I.n_sp;
+        if (n_gap) n_gap[i] = I.n_gap;
+        if (z_min) z_min[i] = I.zmin;
+        if (z_max) z_max[i] = I.zmax;
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_set_T(mpr_ctx* c, const double* T, mpr_stream stream) {
+    if (!c || !T) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < c->g.n_img; ++i)
+        if (!(T[i] > 0.0) || !std::isfinite(T[i])) return fail(MPR_ERR_INVALID_ARG, "T must be positive");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double* tmp = c->d_newton;  // 4 doubles per image of room
+    MPR_CUDA(cudaMemcpyAsync(tmp, T, sizeof(double) * c->g.n_img, cudaMemcpyHostToDevice, s));
+    set_T_kernel<<<grid_for(c->g.n_img), 256, 0, s>>>(c->d_img, tmp, c->g.n_img);
+    MPR_CUDA(cudaGetLastError());
+    MPR_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < c->g.n_img; ++i) { c->h_img[i].T = T[i]; c->h_img[i].invT = (float)(1.0 / T[i]); }
+    c->T_set = true;
+    return MPR_OK;
+}
+
+mpr_status mpr_get_T(mpr_ctx* c, double* T, mpr_stream stream) {
+    if (!c || !T) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<ImgDev> h(c->g.n_img);
+    MPR_CUDA(cudaMemcpyAsync(h.data(), c->d_img, sizeof(ImgDev) * c->g.n_img, cudaMemcpyDeviceToHost, s));
+    MPR_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < c->g.n_img; ++i) T[i] = h[i].T;
+    return MPR_OK;
+}
+
+mpr_status mpr_estimate_T(mpr_ctx* c, double* T_out, mpr_stream stream) {
+    if (!c || !c->sub) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    const double J = c->p.J;
+    for (int i = 0; i < c->g.n_img; ++i) {
+        const ImgDev& I = c->h_img[i];
+        if (I.n_sp == 0) return fail(MPR_ERR_NO_SAMPLE_PAIRS, "image " + std::to_string(i) + " has no sample pairs");
+        if (!(I.e_s > -J && I.e_s < -4.0 * J / (kPiD * kPiD)))
+            return fail(MPR_ERR_T_OUT_OF_RANGE, "image " + std::to_string(i) +
+                                                    ": e_s outside (-J, -4J/pi^2)");
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    mpr_ctx* u = c->sub;
+    const int n_img = c->g.n_img;
+    const int K = u->g.n_chains;
+    newton_init_kernel<<<grid_for(n_img), 256, 0, s>>>(u->d_img, c->d_img, c->d_newton, n_img,
+                                                      c->topt.T_lo, c->topt.T_hi, J);
+    MPR_CUDA(cudaGetLastError());
+    for (int it = 0; it < c->topt.iters; ++it) {
+        const int neq = it == 0 ? 2 * c->topt.n_equil : c->topt.n_equil;
+        MPR_TRY(run_sweeps(u, neq, MPR_EQUIL, 0, false, false, s));
+        MPR_TRY(run_sweeps(u, c->topt.n_meas, MPR_MEASURE, MPR_RECORD_ENERGY, true, false, s));
+        newton_kernel<<<grid_for(n_img), 256, 0, s>>>(u->d_img, c->d_img, u->ch, c->d_newton, n_img,
+                                                     K, c->topt.n_meas);
+        MPR_CUDA(cudaGetLastError());
+    }
+    c->T_set = true;
+    if (T_out) MPR_TRY(mpr_get_T(c, T_out, stream));
+    return MPR_OK;
+}
+
+mpr_status mpr_sweep(mpr_ctx* c, int n_sweeps, int phase, int flags, mpr_stream stream) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_sweeps < 0) return fail(MPR_ERR_INVALID_ARG, "n_sweeps < 0");
+    if (phase != MPR_EQUIL && phase != MPR_MEASURE) return fail(MPR_ERR_INVALID_ARG, "bad phase");
+    if (!c->T_set) return fail(MPR_ERR_STATE, "temperature not set: call mpr_estimate_T or mpr_set_T");
+    return run_sweeps(c, n_sweeps, phase, flags, false, true, reinterpret_cast<cudaStream_t>(stream));
+}
+
+mpr_status mpr_energy(mpr_ctx* c, double* e_out, mpr_mem where, mpr_stream stream) {
+    if (!c || !e_out) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int nc = c->g.n_img * c->g.n_chains;
+    double* d_out = where == MPR_DEVICE ? e_out : c->d_eout;
+    MPR_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double) * nc, s));
+    long long maxn = 0;
+    for (int i = 0; i < c->g.n_img; ++i) maxn = std::max(maxn, (long long)c->g.Lx[i] * c->g.Ly[i]);
+    energy_kernel<<<dim3(grid_for(maxn, 256, 512), nc), 256, 0, s>>>(
+        c->d_img, c->d_state, c->d_samp, c->d_slot_map, c->g.path == MPR_PATH_TILED ? 1 : 0,
+        c->g.n_chains, (float)c->p.q, (float)c->p.J, d_out);
+    MPR_CUDA(cudaGetLastError());
+    energy_finish_kernel<<<grid_for(nc), 256, 0, s>>>(c->d_img, d_out, c->g.n_chains, nc);
+    MPR_CUDA(cudaGetLastError());
+    if (where == MPR_HOST) {
+        MPR_CUDA(cudaMemcpyAsync(e_out, d_out, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaStreamSynchronize(s));
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_predict(mpr_ctx* c, float* z_hat, float* z_std, mpr_mem where, mpr_stream stream) {
+    if (!c || !z_hat) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (c->n_meas_done == 0) return fail(MPR_ERR_STATE, "no measurement sweep has run");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t N = (size_t)c->g.n_sites;
+    float* dh = where == MPR_DEVICE ? z_hat : c->d_out;
+    float* ds = where == MPR_DEVICE ? z_std : (z_std ? c->d_out + N : nullptr);
+    long long maxn = 0;
+    for (int i = 0; i < c->g.n_img; ++i) maxn = std::max(maxn, (long long)c->g.Lx[i] * c->g.Ly[i]);
+    predict_kernel<<<dim3(grid_for(maxn, 256, 2048), c->g.n_img), 256, 0, s>>>(
+        c->d_img, c->d_acc1, c->d_acc2, c->d_zst, c->d_slot_map, c->d_samp,
+        c->g.path == MPR_PATH_TILED ? 1 : 0, (double)c->n_meas_done * c->g.n_chains, dh, ds);
+    MPR_CUDA(cudaGetLastError());
+    if (where == MPR_HOST) {
+        MPR_CUDA(cudaMemcpyAsync(z_hat, dh, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+        if (z_std) MPR_CUDA(cudaMemcpyAsync(z_std, ds, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaStreamSynchronize(s));
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_reset_accumulators(mpr_ctx* c, mpr_stream stream) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MPR_CUDA(cudaMemsetAsync(c->d_acc1, 0, sizeof(double) * c->L.n_slots, s));
+    MPR_CUDA(cudaMemsetAsync(c->d_acc2, 0, sizeof(double) * c->L.n_slots, s));
+    c->n_meas_done = 0;
+    return MPR_OK;
+}
+
+static mpr_status state_copy(mpr_ctx* c, float* phi, mpr_mem where, int dir, cudaStream_t s) {
+    const int tiled = c->g.path == MPR_PATH_TILED ? 1 : 0;
+    const int nc = c->g.n_img * c->g.n_chains;
+    if (where == MPR_DEVICE) {
+        long long maxn = 0;
+        for (int i = 0; i < c->g.n_img; ++i) maxn = std::max(maxn, (long long)c->g.Lx[i] * c->g.Ly[i]);
+        state_copy_kernel<<<dim3(grid_for(maxn, 256, 1024), nc), 256, 0, s>>>(
+            c->d_img, c->d_state, c->d_samp, c->d_slot_map, tiled, c->g.n_chains, phi, dir, 0,
+            nullptr);
+        MPR_CUDA(cudaGetLastError());
+        return MPR_OK;
+    }
+    // host buffers: one (image, chain) plane at a time through the output staging area
+    float* stage = c->d_out;
+    for (int ic = 0; ic < nc; ++ic) {
+        const int im = ic / c->g.n_chains, chain = ic - im * c->g.n_chains;
+        const long long n = (long long)c->g.Lx[im] * c->g.Ly[im];
+        float* h = phi + c->g.site_off[im] * c->g.n_chains + (long long)chain * n;
+        if (dir == 1) MPR_CUDA(cudaMemcpyAsync(stage, h, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        state_copy_kernel<<<dim3(grid_for(n, 256, 1024), 1), 256, 0, s>>>(
+            c->d_img, c->d_state, c->d_samp, c->d_slot_map, tiled, c->g.n_chains, nullptr, dir, ic,
+            stage);
+        MPR_CUDA(cudaGetLastError());
+        if (dir == 0) MPR_CUDA(cudaMemcpyAsync(h, stage, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    }
+    MPR_CUDA(cudaStreamSynchronize(s));
+    return MPR_OK;
+}
+
+mpr_status mpr_get_state(mpr_ctx* c, float* phi, mpr_mem where, mpr_stream stream) {
+    if (!c || !phi) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    return state_copy(c, phi, where, 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+mpr_status mpr_set_state(mpr_ctx* c, const float* phi, mpr_mem where, mpr_stream stream) {
+    if (!c || !phi) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    return state_copy(c, const_cast<float*>(phi), where, 1, reinterpret_cast<cudaStream_t>(stream));
+}
+
+mpr_status mpr_get_chain_info(mpr_ctx* c, float* a, uint32_t* accepted, double* e_last,
+                              mpr_stream stream) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int nc = c->g.n_img * c->g.n_chains;
+    if (a) MPR_CUDA(cudaMemcpyAsync(a, c->ch.a, sizeof(float) * nc, cudaMemcpyDeviceToHost, s));
+    if (accepted) MPR_CUDA(cudaMemcpyAsync(accepted, c->ch.acc_last, sizeof(uint32_t) * nc, cudaMemcpyDeviceToHost, s));
+    if (e_last) MPR_CUDA(cudaMemcpyAsync(e_last, c->ch.e_last, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    MPR_CUDA(cudaStreamSynchronize(s));
+    return MPR_OK;
+}
+
+mpr_status mpr_set_chain_a(mpr_ctx* c, const float* a, mpr_stream stream) {
+    if (!c || !a) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    const int nc = c->g.n_img * c->g.n_chains;
+    for (int i = 0; i < nc; ++i)
+        if (!(a[i] >= 1.0f) || !std::isfinite(a[i])) return fail(MPR_ERR_INVALID_ARG, "a must be >= 1");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MPR_CUDA(cudaMemcpyAsync(c->ch.a, a, sizeof(float) * nc, cudaMemcpyHostToDevice, s));
+    MPR_CUDA(cudaStreamSynchronize(s));
+    return MPR_OK;
+}
+
+mpr_status mpr_get_sweep_index(const mpr_ctx* c, uint32_t* sweep, uint32_t* equil_index) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    if (sweep) *sweep = c->sweep;
+    if (equil_index) *equil_index = c->equil_index;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_sweep_index(mpr_ctx* c, uint32_t sweep, uint32_t equil_index, mpr_stream stream) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    Control h{sweep, equil_index, 0u, 0u};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MPR_CUDA(cudaMemcpyAsync(c->d_ctl, &h, sizeof(Control), cudaMemcpyHostToDevice, s));
+    MPR_CUDA(cudaStreamSynchronize(s));
+    c->sweep = sweep;
+    c->equil_index = equil_index;
+    return MPR_OK;
+}
+
+void mpr_destroy(mpr_ctx* c) { delete c; }
+
+}  // extern "C"

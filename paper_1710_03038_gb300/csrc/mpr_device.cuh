@@ -1,0 +1,169 @@
+// Device-side building blocks shared by the MPR kernels: the counter-based
+// random stream, the hybrid single-site update of Alg. 1 and small math
+// helpers.  Everything here is single precision except where noted.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpr {
+
+constexpr float kTwoPi = 6.28318530717958647692f;    // rounds up: 6.2831855f
+constexpr float kInvTwoPi = 0.15915494309189533577f;
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kFieldEps2 = 1e-24f;                   // |field| < 1e-12: no reflection
+
+// --------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 -> 64-bit
+// products, Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 24-bit uniform in [0, 1), exact in FP32.
+__device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+
+// The random stream's counter for site (x, y) of colour `colour`: one Philox
+// call per two same-colour sites of a row (packed column k = x >> 1, pair
+// k >> 1).  sweep = 0xFFFFFFFF is the hot start.
+__device__ __forceinline__ uint4 site_counter(int x, int y, int colour, uint32_t sweep,
+                                              uint32_t chain, uint32_t img) {
+    const uint32_t k = (uint32_t)x >> 1;
+    return make_uint4(((uint32_t)y << 16) | (k >> 1), sweep, chain,
+                      img | ((uint32_t)colour << 31));
+}
+
+// (u, r) of a site: words 0-1 for an even packed column, 2-3 for an odd one.
+__device__ __forceinline__ void site_uniform_words(int x, int y, int colour, uint32_t sweep,
+                                                   uint32_t chain, uint32_t img, uint2 key,
+                                                   uint32_t& wu, uint32_t& wr) {
+    const uint4 w = philox4x32_10(site_counter(x, y, colour, sweep, chain, img), key);
+    const bool odd = ((uint32_t)x >> 1) & 1u;
+    wu = odd ? w.z : w.x;
+    wr = odd ? w.w : w.y;
+}
+
+// ---------------------------------------------------------- small math
+// sin(t) for |t| <= pi/2 from its Taylor series through t^13 (relative error
+// below one ulp on that interval); used for the half proposal step where the
+// hardware sine's absolute error would dominate.
+__device__ __forceinline__ float sin_taylor(float t) {
+    const float t2 = t * t;
+    float p = -1.0f / 6227020800.0f;          // -1/13!
+    p = fmaf(p, t2, 1.0f / 39916800.0f);       //  1/11!
+    p = fmaf(p, t2, -1.0f / 362880.0f);        // -1/9!
+    p = fmaf(p, t2, 1.0f / 5040.0f);           //  1/7!  (sign pattern of sin)
+    p = fmaf(p, t2, -1.0f / 120.0f);
+    p = fmaf(p, t2, 1.0f / 6.0f);
+    // sin t = t - t^3/3! + t^5/5! - ...  = t * (1 - t2 * (1/3! - t2 * (1/5! - ...)))
+    return t * fmaf(-t2, p, 1.0f);
+}
+
+// Wraps an angle from (-3 pi, 3 pi) into [-pi, pi].
+__device__ __forceinline__ float wrap_pi(float v) {
+    if (v > kPi) v -= kTwoPi;
+    else if (v < -kPi) v += kTwoPi;
+    return v;
+}
+
+// ------------------------------------------------------ hybrid update
+struct UpdateConst {
+    float q, inv_q, two_pi_q, J;
+};
+
+struct UpdateOut {
+    float phi;      // new angle
+    float R;        // local field length |sum_j exp(i q phi_j)|
+    float x_new;    // q * phi_new - Psi (site energy = -J R cos(x_new))
+    bool accepted;
+};
+
+// One application of Alg. 1 to a gap site with angle phi whose neighbours
+// give the field (C, S) = sum_j (cos q phi_j, sin q phi_j).
+//  1. over-relaxation (Eq. over-relax, q-consistent): Psi = atan2(S, C),
+//     theta' = (2 Psi - q phi) mod 2 pi, phi' = theta'/q if theta' < 2 pi q;
+//  2-3. proposal phi'' = (phi' + alpha (u - 1/2)) mod 2 pi, alpha = 2 pi / a;
+//  4. dH = -J R [cos(q phi'' - Psi) - cos(q phi' - Psi)]
+//        = 2 J R sin(x + h) sin(h), x = q phi' - Psi, h = q (phi'' - phi') / 2
+//     (product form: no cancellation for small steps);
+//  5-6. accept iff r < exp(-dH / T) (always when dH <= 0).
+__device__ __forceinline__ UpdateOut hybrid_update(float phi, float C, float S, uint32_t wu,
+                                                   uint32_t wr, const UpdateConst& k,
+                                                   float alpha, float invT) {
+    const float R2 = fmaf(C, C, S * S);
+    float Psi = 0.0f;
+    float phi1 = phi;
+    if (R2 > kFieldEps2) {
+        Psi = atan2f(S, C);
+        float t = fmaf(2.0f, Psi, -k.q * phi);
+        t = fmaf(-kTwoPi, floorf(t * kInvTwoPi), t);
+        if (t >= 0.0f && t < k.two_pi_q) phi1 = t * k.inv_q;
+    }
+    const float R = sqrtf(R2);
+    const float u = u24(wu);
+    const float r = u24(wr);
+    float phi2 = fmaf(alpha, u - 0.5f, phi1);
+    if (phi2 < 0.0f) phi2 += kTwoPi;
+    else if (phi2 >= kTwoPi) phi2 -= kTwoPi;
+    const float x = fmaf(k.q, phi1, -Psi);
+    const float h = 0.5f * k.q * (phi2 - phi1);
+    const float s1 = __sinf(wrap_pi(x + h));
+    const float s2 = sin_taylor(h);
+    const float dH = 2.0f * k.J * R * s1 * s2;
+    const bool acc = (dH <= 0.0f) || (r < __expf(-dH * invT));
+    UpdateOut o;
+    o.phi = acc ? phi2 : phi1;
+    o.R = R;
+    o.x_new = acc ? x + 2.0f * h : x;
+    o.accepted = acc;
+    return o;
+}
+
+// Energy of a site after its update: -J R cos(x_new).
+__device__ __forceinline__ float site_energy_after(const UpdateOut& o, float J) {
+    return -J * o.R * __cosf(wrap_pi(o.x_new));
+}
+
+// --------------------------------------------------------- reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned warp_sum(unsigned v) {
+    return __reduce_add_sync(0xffffffffu, v);
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sample sites are stored with the sign bit set (-0.0f encodes angle 0).
+__device__ __forceinline__ bool is_fixed(float v) { return __float_as_uint(v) >> 31; }
+__device__ __forceinline__ float angle_of(float v) { return fabsf(v); }
+__device__ __forceinline__ float as_fixed(float phi) {
+    return __uint_as_float(__float_as_uint(phi) | 0x80000000u);
+}
+
+}  // namespace mpr

@@ -1,0 +1,102 @@
+// Host/device shared layout of an MPR context and the launchers that the
+// translation units of the library provide to each other.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mpr.h"
+
+namespace mpr {
+
+// Tile of the tiled path.  Origins are multiples of the (even) tile sizes,
+// so the colour of extended-tile cell (xx, yy) is (xx + yy) & 1.
+struct TileDesc {
+    int img;
+    int x0, y0;
+    int off[2];       // slot offset of the colour-c gap segment inside the image's slot space
+    int cnt[2];       // gap sites of colour c in the tile
+    int halo_cnt[2];  // other-colour gap sites in the 1-ring seen by the colour-c pass
+};
+
+// Per image, in device memory.
+struct ImgDev {
+    int Lx, Ly;
+    long long site_off;   // offset in concatenated [sum Lx*Ly] arrays
+    long long state_off;  // float offset of chain 0 in the state buffer
+    long long stride;     // floats between consecutive chains
+    long long slot_off;   // tiled: offset in the slot arrays (acc, slot_pos); plain: site_off
+    int tile0, ntiles;
+    float zmin, zmax;
+    float invT, pad0;
+    double T, e_s, E_ss, n_bonds;
+    long long n_gap, n_sp;
+};
+
+// Device-resident counters of a context.
+struct Control {
+    uint32_t sweep;        // Philox sweep field of the next sweep
+    uint32_t equil_index;  // i of Alg. 2 step 4.2 for the next equilibration sweep
+    uint32_t status;       // device-side error bits
+    uint32_t pad;
+};
+
+// Per-chain device arrays (length n_img * n_chains, image-major).
+struct ChainDev {
+    float* a;
+    uint32_t* acc_cnt;    // accepted proposals of the sweep in progress
+    uint32_t* acc_last;   // of the last completed sweep
+    double* e_cur;        // bond energy (gap-related part) reduced during the sweep
+    double* e_last;       // H / N_GP after the last recorded sweep
+    double* e_sum;        // sums of e over measurement sweeps (temperature estimate)
+    double* e_sum2;
+};
+
+enum SweepFlags : int {
+    kEnergy = 1,       // reduce the energy this pass
+    kAccumulate = 2,   // add the new angles to the realisation accumulators
+    kAccumulate2 = 4,  // also squares
+    kAlphaOne = 8,     // a = 1 (printed Alg. 2 step 5.2)
+};
+
+struct SweepArgs {
+    const ImgDev* img;
+    const TileDesc* tiles;      // tiled path
+    const uint32_t* slot_pos;   // tiled: (y << 16) | x per slot, 0xFFFFFFFF for padding
+    const int2* halo;           // tiled: [tile][2][cap] (slot, cs index)
+    const float* samp;          // tiled: sample angle per site (>= 0) or -1 at gaps
+    float* state;
+    double* acc1;
+    double* acc2;
+    ChainDev ch;
+    const Control* ctl;
+    uint2 key;
+    float q, inv_q, two_pi_q, J;
+    int n_chains;
+    int chain_group;
+    int colour;
+    int flags;
+    int halo_cap;
+    int n_img;
+    uint32_t img_tag;          // OR-ed into the image field of the counter (1 << 30: T lattices)
+};
+
+// ---- launchers ------------------------------------------------------------
+cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tile_x, int tile_y,
+                              cudaStream_t s);
+cudaError_t launch_plain_pass(const SweepArgs& a, int max_Lx, int max_Ly, cudaStream_t s);
+bool tiled_config_supported(int tile_x, int tile_y);
+
+// tile-table construction (tiled path)
+cudaError_t launch_tile_count(const ImgDev* img, const TileDesc* tiles, int n_tiles,
+                              const uint8_t* gap, int tile_x, int tile_y, int* counts,
+                              cudaStream_t s);
+cudaError_t launch_tile_fill(const ImgDev* img, const TileDesc* tiles, int n_tiles,
+                             const uint8_t* gap, int tile_x, int tile_y, uint32_t* slot_pos,
+                             int* slot_map, int2* halo, int halo_cap, cudaStream_t s);
+
+}  // namespace mpr

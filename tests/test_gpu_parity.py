@@ -1,0 +1,338 @@
+"""Parity of the CUDA path against the FP64 oracle (needs a GPU).
+
+Sweep-by-sweep parity: the GPU and the oracle start every sweep from the same
+state (the oracle's, rounded to FP32), the same random stream and the same a,
+T.  Angles must agree within 1e-5 rad except at sites whose decision lay
+within the FP32 error bound of its threshold (counted, below 1e-4 of the
+sites) and their downstream neighbours in the same sweep.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1710_03038_gb300 as mpr  # noqa: E402
+
+TWO_PI = 2 * math.pi
+ANGLE_TOL = 1e-5          # rad, spec tolerance for angles
+NEAR_FRAC_MAX = 1e-4      # near-threshold decisions allowed per site
+SEED = 0x5EED1234ABCD
+
+
+def near_threshold(diag, gap):
+    """Sites whose FP64 decision lies within the FP32 error bound of a threshold.
+
+    FP32 angle errors are a few ulp of 2 pi (~2e-6 rad bound); the Metropolis
+    test compares r with exp(-dH/T), whose FP32 error is bounded by
+    AP * (sens * 2e-6 + |dH/T| * 1e-5) where sens bounds d(dH/T)/dphi.  The
+    over-relaxation range test, the proposal wrap and a vanishing local field
+    are decisions too.
+    """
+    ap = np.nan_to_num(diag["ap"])
+    bound = 1e-6 + ap * (np.nan_to_num(diag["sens"]) * 2e-6 + np.abs(np.nan_to_num(diag["dH_over_T"])) * 1e-5)
+    near = np.abs(np.nan_to_num(diag["r_minus_ap"], nan=1.0)) <= bound
+    near |= np.nan_to_num(diag["or_slack"], nan=1.0) < 1e-5
+    near |= np.nan_to_num(diag["wrap_slack"], nan=1.0) < 1e-5
+    near |= np.nan_to_num(diag["field"], nan=1.0) < 1e-5
+    return near & (gap == 1)
+
+
+def taint(near, gap):
+    """Near sites plus the second-colour neighbours of first-colour near sites."""
+    Ly, Lx = gap.shape
+    yy, xx = np.mgrid[0:Ly, 0:Lx]
+    red = ((xx + yy) & 1) == 0
+    t = near.copy()
+    rn = near & red
+    t[1:, :] |= rn[:-1, :]
+    t[:-1, :] |= rn[1:, :]
+    t[:, 1:] |= rn[:, :-1]
+    t[:, :-1] |= rn[:, 1:]
+    return t
+
+
+def compare_sweep(before, after_gpu, gap, *, T, a, seed, img, chain, sweep_index):
+    ref, n_acc, diag = oracle.sweep(before.astype(np.float64), gap, T=T, a=float(a), seed=seed,
+                                    img=img, chain=chain, sweep_index=sweep_index,
+                                    diagnostics=True)
+    near = near_threshold(diag, gap)
+    tainted = taint(near, gap)
+    d = np.abs(ref - after_gpu.astype(np.float64))
+    bad = (d > ANGLE_TOL) & (gap == 1) & ~tainted
+    assert not bad.any(), (f"{bad.sum()} sites differ beyond {ANGLE_TOL} without a near-threshold "
+                           f"decision; worst {d[bad].max():.3e}")
+    # sample sites never move
+    assert np.array_equal(after_gpu[gap == 0], before[gap == 0])
+    return ref, n_acc, int(near.sum()), float(d[(gap == 1) & ~tainted].max(initial=0.0))
+
+
+def ragged_images():
+    shapes = [(64, 64), (37, 53), (70, 31), (5, 130)]
+    zs, gs = [], []
+    for k, (h, w) in enumerate(shapes):
+        z = synthetic.grf((h, w), nu=0.5, ell=6.0, mean=50, std=10, seed=100 + k)
+        g = synthetic.uniform_gaps((h, w), 0.25 + 0.15 * k, 200 + k)
+        zs.append(z.astype(np.float32))
+        gs.append(g.astype(np.uint8))
+    # one image with a block gap
+    gs[0][10:30, 20:44] = 1
+    return zs, gs
+
+
+def make_ctx(zs, gs, chains, path="tiled", **kw):
+    return mpr.Context(zs, gs, chains=chains, params=mpr.Params(seed=SEED, path=path, **kw))
+
+
+# ------------------------------------------------------------------ RNG
+
+def test_philox_matches_known_answers_and_toolkit(golden_dir):
+    rows = []
+    with open(f"{golden_dir}/philox4x32_10_kat.txt") as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(t, 16) for t in line.split()])
+    for r in rows:
+        out = mpr.philox(np.array([r[0:4]], dtype=np.uint32), r[4:6])
+        assert list(out[0]) == r[6:10]
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = [0xDEADBEEF, 0x12345678]
+    mine = mpr.philox(ctr, key)
+    ref = mpr.philox(ctr, key, reference=True)
+    assert np.array_equal(mine, ref)
+    o = np.array([oracle.philox4x32_10(c, key) for c in ctr[:64]])
+    assert np.array_equal(mine[:64], o)
+
+
+# ------------------------------------------------------------- init
+
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_init_map_hot_start_and_sample_energy(path):
+    zs, gs = ragged_images()
+    R = 3
+    ctx = make_ctx(zs, gs, R, path)
+    info = ctx.image_info()
+    st = [s.cpu().numpy() for s in ctx.get_state()]
+    for i, (z, g) in enumerate(zip(zs, gs)):
+        phi, zmin, zmax = oracle.map_to_angles(z.astype(np.float64), g)
+        assert info["zmin"][i] == zmin and info["zmax"][i] == zmax
+        assert info["n_gap"][i] == g.sum()
+        e_s, nsp = oracle.sample_energy(phi, g)
+        assert info["n_sp"][i] == nsp
+        assert abs(info["e_s"][i] - e_s) < 1e-6
+        for c in range(R):
+            ref = oracle.hot_start(phi, g, SEED, i, c)
+            assert np.max(np.abs(st[i][c] - ref)) < 1e-6
+
+
+# ---------------------------------------------------- sweep by sweep
+
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_sweep_by_sweep_parity_ragged_batch(path):
+    zs, gs = ragged_images()
+    R = 3
+    ctx = make_ctx(zs, gs, R, path)
+    T = np.array([0.15, 0.3, 0.08, 0.5])
+    ctx.set_T(T)
+    state = [s.cpu().numpy().astype(np.float64) for s in ctx.get_state()]
+    n_sites = sum(g.size for g in gs) * R
+    near_total = 0
+    a_vals = ctx.chain_info()["a"]
+    for k in range(6):
+        ctx.set_state([s.astype(np.float32) for s in state])
+        before = [s.astype(np.float32) for s in state]
+        sweep_idx, eq_idx = ctx.sweep_index()
+        ctx.sweep(1, "equil", record_energy=True)
+        after = [s.cpu().numpy() for s in ctx.get_state()]
+        info = ctx.chain_info()
+        for i, g in enumerate(gs):
+            for c in range(R):
+                ref, n_acc, n_near, worst = compare_sweep(
+                    before[i][c], after[i][c], g, T=T[i], a=a_vals[i, c], seed=SEED, img=i,
+                    chain=c, sweep_index=sweep_idx)
+                near_total += n_near
+                assert abs(int(info["accepted"][i, c]) - n_acc) <= n_near
+                # the a-adaptation (Alg. 2 step 4.2) from the GPU's own count
+                a_ref = oracle.adapt_a(float(a_vals[i, c]), int(info["accepted"][i, c]),
+                                       int(g.sum()), eq_idx)
+                assert abs(info["a"][i, c] - a_ref) < 1e-6 * a_ref
+                # energy recorded after the sweep vs the oracle energy of the GPU state
+                e_ref = oracle.specific_energy(after[i][c].astype(np.float64))
+                assert abs(info["e_last"][i, c] - e_ref) < 2e-6
+                state[i][c] = ref
+        a_vals = info["a"]
+    assert near_total <= NEAR_FRAC_MAX * n_sites * 6 + 2
+
+
+def test_tiled_and_plain_paths_agree_bitwise():
+    zs, gs = ragged_images()
+    R = 4
+    outs = []
+    for path in ("tiled", "plain"):
+        ctx = make_ctx(zs, gs, R, path)
+        ctx.set_T([0.2, 0.2, 0.1, 0.4])
+        ctx.sweep(8, "equil")
+        ctx.sweep(4, "measure")
+        outs.append(([s.cpu().numpy() for s in ctx.get_state()],
+                     [p.cpu().numpy() for p in ctx.predict()]))
+    for a, b in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert np.allclose(a, b, rtol=1e-6, atol=1e-5)
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 32), (64, 64), (128, 32)])
+def test_tile_shapes_and_chain_groups_agree_bitwise(tile):
+    zs, gs = ragged_images()
+    R = 5
+    ref = make_ctx(zs, gs, R, "plain")
+    ref.set_T([0.2, 0.2, 0.1, 0.4])
+    ref.sweep(3, "equil")
+    want = [s.cpu().numpy() for s in ref.get_state()]
+    for cg in (1, 2, 5):
+        ctx = make_ctx(zs, gs, R, "tiled", tile=tile, chain_group=cg)
+        ctx.set_T([0.2, 0.2, 0.1, 0.4])
+        ctx.sweep(3, "equil")
+        got = [s.cpu().numpy() for s in ctx.get_state()]
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+
+
+def test_determinism_same_state_same_result():
+    """Colour-race canary: the same sweep from the same state gives identical bits."""
+    zs, gs = ragged_images()
+    ctx = make_ctx(zs, gs, 4)
+    ctx.set_T([0.2, 0.2, 0.1, 0.4])
+    ctx.sweep(2, "equil")
+    s0 = [s.clone() for s in ctx.get_state()]
+    idx = ctx.sweep_index()
+    ctx.sweep(1, "equil")
+    r1 = [s.clone() for s in ctx.get_state()]
+    ctx.set_state(s0)
+    ctx.set_sweep_index(*idx)
+    ctx.sweep(1, "equil")
+    r2 = ctx.get_state()
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+
+
+# ------------------------------------------------------------ energy
+
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_energy_matches_oracle(path):
+    zs, gs = ragged_images()
+    ctx = make_ctx(zs, gs, 3, path)
+    ctx.set_T([0.2, 0.2, 0.1, 0.4])
+    ctx.sweep(5, "equil", record_energy=True)
+    e = ctx.energy()
+    st = ctx.get_state()
+    rec = ctx.chain_info()["e_last"]
+    for i in range(len(gs)):
+        for c in range(3):
+            ref = oracle.specific_energy(st[i][c].cpu().numpy().astype(np.float64))
+            assert abs(e[i, c] - ref) < 1e-6
+            assert abs(rec[i, c] - ref) < 2e-6
+
+
+def test_energy_autograd_matches_finite_differences_and_oracle():
+    rng = np.random.default_rng(3)
+    phi_np = rng.uniform(0, TWO_PI, (2, 24, 31))
+    phi = torch.tensor(phi_np, dtype=torch.float32, device="cuda", requires_grad=True)
+    J = torch.tensor(1.3, dtype=torch.float64, requires_grad=True)
+    H = mpr.MPREnergy.apply(phi, J)
+    w = torch.tensor([0.7, -1.1], dtype=torch.float64, device="cuda")
+    (H * w).sum().backward()
+    for k in range(2):
+        p64 = phi.detach()[k].cpu().numpy().astype(np.float64)
+        assert abs(H[k].item() - oracle.energy(p64, J=1.3)) < 1e-4 * abs(H[k].item()) + 1e-4
+        g_ref = oracle.torque(p64, J=1.3) * w[k].item()
+        assert np.max(np.abs(phi.grad[k].cpu().numpy() - g_ref)) < 1e-5
+        # central differences (h = 1e-3, FP64) on a few sites
+        for (y, x) in [(0, 0), (5, 7), (23, 30), (12, 0)]:
+            a = p64.copy(); a[y, x] += 1e-3
+            b = p64.copy(); b[y, x] -= 1e-3
+            fd = (oracle.energy(a, J=1.3) - oracle.energy(b, J=1.3)) / 2e-3 * w[k].item()
+            assert abs(phi.grad[k, y, x].item() - fd) < 1e-5
+    dJ = sum(w[k].item() * oracle.energy(phi.detach()[k].cpu().numpy().astype(np.float64)) / 1.3
+             for k in range(2))
+    assert abs(J.grad.item() - dJ) < 1e-4 * abs(dJ) + 1e-4
+
+
+# ------------------------------------------------ long runs, statistics
+
+def test_long_run_statistics_and_prediction_grf64():
+    """Config 1 (64 x 64 GRF, 33% gaps, 10 chains, 200 + 100 sweeps) at fixed T:
+    mean specific energy within 3 sigma and MAE/RMSE within 2% of the oracle."""
+    w = synthetic.workload("grf64")
+    z, g = w.z[0], w.gap[0]
+    T = 0.13
+    R, ne, nm = w.chains, w.n_equil, w.n_meas
+    ctx = make_ctx([z], [g], R)
+    ctx.set_T([T])
+    ctx.sweep(ne, "equil")
+    es = []
+    for _ in range(nm):
+        ctx.sweep(1, "measure", record_energy=True)
+        es.append(ctx.chain_info()["e_last"][0])
+    es = np.array(es)                      # [nm, R]
+    zh = ctx.predict()[0].cpu().numpy()
+    phi, zmin, zmax = oracle.map_to_angles(z.astype(np.float64), g)
+    sim = oracle.simulate(phi, g, T=T, R=R, n_equil=ne, n_meas=nm, seed=SEED + 1, history=True)
+    e_or = sim["e_hist"][:, ne:]           # [R, nm]
+    # chains are independent: sigma from the spread of chain means
+    m_g, m_o = es.mean(0), e_or.mean(1)
+    sig = math.sqrt(m_g.var(ddof=1) / R + m_o.var(ddof=1) / R)
+    assert abs(m_g.mean() - m_o.mean()) < 3 * sig + 1e-6, (m_g.mean(), m_o.mean(), sig)
+    zo = oracle.unmap(sim["phi_mean"], zmin, zmax)
+    truth = z.astype(np.float64)
+    m = g == 1
+    mae_g, mae_o = np.mean(np.abs(zh[m] - truth[m])), np.mean(np.abs(zo[m] - truth[m]))
+    rmse_g = math.sqrt(np.mean((zh[m] - truth[m]) ** 2))
+    rmse_o = math.sqrt(np.mean((zo[m] - truth[m]) ** 2))
+    assert abs(mae_g - mae_o) < 0.02 * mae_o, (mae_g, mae_o)
+    assert abs(rmse_g - rmse_o) < 0.02 * rmse_o, (rmse_g, rmse_o)
+    # sample pixels are returned unchanged
+    assert np.array_equal(zh[~m], z[~m])
+
+
+def test_estimate_T_newton_matches_oracle_bisection():
+    """SEM temperature: GPU Newton (fluctuation relation) vs oracle bisection within 1%."""
+    w = synthetic.workload("grf64")
+    z, g = w.z[0], w.gap[0]
+    topts = mpr.TOpts(L=64, chains=4, n_equil=60, n_meas=120, iters=6)
+    ctx = mpr.Context([z], [g], chains=2, params=mpr.Params(seed=SEED), topts=topts)
+    T_gpu = ctx.estimate_T()[0]
+    e_s = ctx.image_info()["e_s"][0]
+    T_or = oracle.estimate_T(e_s, L=64, K=2, n_eq=120, n_meas=120, seed=SEED, rel_tol=2e-3)
+    assert abs(T_gpu - T_or) < 0.01 * T_or, (T_gpu, T_or)
+
+
+# ------------------------------------------------------------ errors
+
+def test_host_errors():
+    z = np.full((8, 8), 3.0, np.float32)
+    g = np.zeros((8, 8), np.uint8)
+    g[0, 0] = 1
+    with pytest.raises(mpr._lib.MprError) as e:
+        mpr.Context([z], [g], chains=2)
+    assert e.value.status == 3  # degenerate range
+    z2 = np.arange(64, dtype=np.float32).reshape(8, 8)
+    cb = np.fromfunction(lambda y, x: (x + y) % 2, (8, 8)).astype(np.uint8)
+    ctx = mpr.Context([z2], [cb], chains=2)
+    with pytest.raises(mpr._lib.MprError) as e:
+        ctx.estimate_T()
+    assert e.value.status == 4  # no sample pairs
+    with pytest.raises(mpr._lib.MprError) as e:
+        ctx.sweep(1)
+    assert e.value.status == 7  # T not set
+    with pytest.raises(mpr._lib.MprError):
+        ctx.predict()
