@@ -159,7 +159,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    w = synthetic.workload("lognormal4096")
+    w = synthetic.workload("lognormal4096", L=args.size)
     z_h, g_h = w.z[0], w.gap[0]
     R, ne, nm = w.chains, w.n_equil, w.n_meas
     P = int(g_h.sum())
@@ -177,7 +177,10 @@ def run_gpu(args):
 
     def step(z_in, g_in, host_out=None, timed=False):
         ctx = mpr.Context([z_in], [g_in], chains=R, params=params, topts=topts, device=dev)
-        ctx.estimate_T_async()
+        if args.T is None:
+            ctx.estimate_T_async()
+        else:
+            ctx.set_T([args.T])
         ctx.sweep(ne, "equil")
         if timed:
             for _ in range(nm):
@@ -222,16 +225,18 @@ def run_gpu(args):
     clocks = clk.stop()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
-    zh_out = torch.empty(N, dtype=torch.float32).pin_memory()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(z_pin, g_pin, host_out=zh_out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
+    ms_e2e = float("nan")
+    if not args.no_e2e:
+        zh_out = torch.empty(N, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(z_pin, g_pin, host_out=zh_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1)
 
     if ws > 1:
         import torch.distributed as dist
@@ -315,6 +320,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--path", default="tiled", choices=["tiled", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--size", type=int, default=4096,
+                    help="image side (4096 is the benchmark; smaller sides are for profiler captures)")
+    ap.add_argument("--T", type=float, default=None,
+                    help="fixed temperature instead of the estimate (profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

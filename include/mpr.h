@@ -221,6 +221,15 @@ mpr_status mpr_lattice_torque(int n, const int* Lx, const int* Ly, const float* 
 mpr_status mpr_philox(int n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                       int reference, mpr_stream stream);
 
+/* Evaluates one of the library's own single-precision approximations, or the
+ * CUDA math routine it stands in for, on n inputs (device float arrays), so
+ * that tests can bound their error: fn 0 = the atan2 used by the
+ * over-relaxation step, atan2(a, b); 1 = CUDA atan2f(a, b); 2 = the series
+ * sine used for half proposal steps, sin(a) for |a| <= pi/2; 3 = CUDA sinf(a).
+ * b may be NULL for fn 2-3.  Asynchronous. */
+mpr_status mpr_math_probe(int fn, int n, const float* a, const float* b, float* out,
+                          mpr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

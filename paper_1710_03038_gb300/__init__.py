@@ -331,6 +331,7 @@ class MPREnergy(torch.autograd.Function):
         ctx.q = q
         ctx.J = Jv
         ctx.J_is_tensor = isinstance(J, torch.Tensor)
+        ctx.J_device = J.device if ctx.J_is_tensor else None
         return H
 
     @staticmethod
@@ -339,8 +340,18 @@ class MPREnergy(torch.autograd.Function):
         g_phi = lattice_torque(phi, gH.to(torch.float64), q=ctx.q, J=ctx.J)
         g_J = None
         if ctx.J_is_tensor:
-            g_J = (gH.to(torch.float64) * H / ctx.J).sum().to(torch.float64)
+            g_J = (gH.to(torch.float64) * H / ctx.J).sum().to(ctx.J_device)
         return g_phi, g_J, None
+
+
+def math_probe(fn: int, a: torch.Tensor, b: torch.Tensor = None) -> torch.Tensor:
+    """The library's own approximations (fn 0: atan2, 2: series sine) or CUDA's (1, 3)."""
+    a = a.to(torch.float32).contiguous()
+    bb = b.to(torch.float32).contiguous() if b is not None else None
+    out = torch.empty_like(a)
+    call("mpr_math_probe", int(fn), a.numel(), _ptr(a), _ptr(bb) if bb is not None else None,
+         _ptr(out), _stream_ptr(None))
+    return out
 
 
 def philox(ctr: np.ndarray, key, reference: bool = False) -> np.ndarray:

@@ -16,9 +16,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmpr.so")
 SOURCES = ["mpr_api.cu", "mpr_tiled.cu", "mpr_plain.cu", "mpr_lattice.cu"]
-HEADERS = ["mpr_device.cuh", "mpr_internal.h"]
+HEADERS = ["mpr_device.cuh", "mpr_internal.h", "mpr_async.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC",
+         "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:
@@ -38,8 +39,16 @@ def build(verbose: bool = False, extra_flags=None) -> str:
     nvcc = _nvcc()
     inc = os.path.join(os.path.dirname(HERE), "include")
     deps = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "mpr.h")]
-    dep_time = max(_mtime(d) for d in deps)
     flags = FLAGS + list(extra_flags or [])
+    # a change of flags rebuilds everything
+    stamp = os.path.join(BUILD, "flags.txt")
+    sig = " ".join(ARCH + flags)
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if old != sig:
+        with open(stamp, "w") as f:
+            f.write(sig)
+    deps.append(stamp)
+    dep_time = max(_mtime(d) for d in deps)
 
     def compile_one(src):
         s = os.path.join(CSRC, src)

@@ -568,7 +568,7 @@ void pick_tiles(const mpr_params& p, int n_img, const int* Lx, const int* Ly, in
     (void)n_chains;
     if (mx <= 48) { tx = 32; ty = 16; }
     else if (mx <= 96) { tx = 32; ty = 32; }
-    else { tx = 64; ty = 64; }
+    else { tx = 64; ty = 32; }
 }
 
 int pick_chain_group(const mpr_ctx* c) {
@@ -862,6 +862,10 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
     a.ch = c->ch;
     a.ctl = c->d_ctl;
     a.key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
+    for (int i = 0; i < 10; ++i) {
+        a.rk[2 * i] = a.key.x + (uint32_t)i * 0x9E3779B9u;
+        a.rk[2 * i + 1] = a.key.y + (uint32_t)i * 0xBB67AE85u;
+    }
     a.q = (float)c->p.q;
     a.inv_q = (float)(1.0 / c->p.q);
     a.two_pi_q = (float)(2.0 * kPiD * c->p.q);
@@ -891,6 +895,19 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
     c->sweep += (uint32_t)n;
     if (equil) c->equil_index += (uint32_t)n;
     if (!equil && accumulate) c->n_meas_done += n;
+    return MPR_OK;
+}
+
+// Device-side error bits (a bounded wait that gave up); blocking.
+mpr_status check_device_status(mpr_ctx* c, cudaStream_t s) {
+    uint32_t st[2] = {0u, 0u};
+    MPR_CUDA(cudaMemcpyAsync(&st[0], &c->d_ctl->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    if (c->sub) MPR_CUDA(cudaMemcpyAsync(&st[1], &c->sub->d_ctl->status, sizeof(uint32_t),
+                                         cudaMemcpyDeviceToHost, s));
+    MPR_CUDA(cudaStreamSynchronize(s));
+    if (st[0] | st[1])
+        return fail(MPR_ERR_DEVICE, "a kernel gave up waiting for an asynchronous copy (status " +
+                                        std::to_string(st[0] | st[1]) + ")");
     return MPR_OK;
 }
 
@@ -1039,7 +1056,7 @@ mpr_status mpr_get_T(mpr_ctx* c, double* T, mpr_stream stream) {
     MPR_CUDA(cudaMemcpyAsync(h.data(), c->d_img, sizeof(ImgDev) * c->g.n_img, cudaMemcpyDeviceToHost, s));
     MPR_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < c->g.n_img; ++i) T[i] = h[i].T;
-    return MPR_OK;
+    return check_device_status(c, s);
 }
 
 mpr_status mpr_estimate_T(mpr_ctx* c, double* T_out, mpr_stream stream) {
@@ -1118,6 +1135,7 @@ mpr_status mpr_predict(mpr_ctx* c, float* z_hat, float* z_std, mpr_mem where, mp
         MPR_CUDA(cudaMemcpyAsync(z_hat, dh, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
         if (z_std) MPR_CUDA(cudaMemcpyAsync(z_std, ds, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
         MPR_CUDA(cudaStreamSynchronize(s));
+        return check_device_status(c, s);
     }
     return MPR_OK;
 }
@@ -1179,7 +1197,7 @@ mpr_status mpr_get_chain_info(mpr_ctx* c, float* a, uint32_t* accepted, double* 
     if (accepted) MPR_CUDA(cudaMemcpyAsync(accepted, c->ch.acc_last, sizeof(uint32_t) * nc, cudaMemcpyDeviceToHost, s));
     if (e_last) MPR_CUDA(cudaMemcpyAsync(e_last, c->ch.e_last, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
     MPR_CUDA(cudaStreamSynchronize(s));
-    return MPR_OK;
+    return check_device_status(c, s);
 }
 
 mpr_status mpr_set_chain_a(mpr_ctx* c, const float* a, mpr_stream stream) {

@@ -9,7 +9,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/mpr.h"
+#include "mpr.h"
 
 namespace mpr {
 
@@ -73,8 +73,9 @@ struct SweepArgs {
     double* acc1;
     double* acc2;
     ChainDev ch;
-    const Control* ctl;
+    Control* ctl;
     uint2 key;
+    uint32_t rk[20];           // Philox round keys k_i = key + i * (0x9E3779B9, 0xBB67AE85)
     float q, inv_q, two_pi_q, J;
     int n_chains;
     int chain_group;

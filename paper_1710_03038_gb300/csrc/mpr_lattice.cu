@@ -78,6 +78,19 @@ __global__ void philox_kernel(int n, const uint32_t* ctr, uint2 key, uint32_t* o
     out[4 * i + 3] = w.w;
 }
 
+__global__ void math_probe_kernel(int fn, int n, const float* a, const float* b, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = 0.0f;
+    switch (fn) {
+        case 0: v = atan2_poly(a[i], b[i]); break;
+        case 1: v = atan2f(a[i], b[i]); break;
+        case 2: v = sin_taylor(a[i]); break;
+        default: v = sinf(a[i]); break;
+    }
+    out[i] = v;
+}
+
 template <typename F>
 mpr_status for_chunks(int n, const int* Lx, const int* Ly, F launch) {
     if (n < 1 || !Lx || !Ly) return MPR_ERR_INVALID_ARG;
@@ -131,6 +144,15 @@ mpr_status mpr_philox(int n, const uint32_t* ctr, const uint32_t* key, uint32_t*
     if (n == 0) return MPR_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     philox_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, ctr, make_uint2(key[0], key[1]), out, reference);
+    return cudaGetLastError() == cudaSuccess ? MPR_OK : MPR_ERR_CUDA;
+}
+
+mpr_status mpr_math_probe(int fn, int n, const float* a, const float* b, float* out,
+                          mpr_stream stream) {
+    if (fn < 0 || fn > 3 || n < 0 || !a || !out || (fn < 2 && !b)) return MPR_ERR_INVALID_ARG;
+    if (n == 0) return MPR_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    math_probe_kernel<<<(n + 255) / 256, 256, 0, s>>>(fn, n, a, b, out);
     return cudaGetLastError() == cudaSuccess ? MPR_OK : MPR_ERR_CUDA;
 }
 

@@ -113,6 +113,26 @@ def test_philox_matches_known_answers_and_toolkit(golden_dir):
     assert np.array_equal(mine[:64], o)
 
 
+def test_own_math_against_cuda_routines():
+    """The library's atan2 and series sine against CUDA atan2f / sinf and FP64."""
+    g = torch.Generator(device="cpu").manual_seed(0)
+    y = (torch.rand(200000, generator=g) * 8 - 4).cuda()
+    x = (torch.rand(200000, generator=g) * 8 - 4).cuda()
+    mine = mpr.math_probe(0, y, x).double().cpu().numpy()
+    cuda = mpr.math_probe(1, y, x).double().cpu().numpy()
+    exact = np.arctan2(y.double().cpu().numpy(), x.double().cpu().numpy())
+    assert np.max(np.abs(mine - exact)) < 4e-7
+    assert np.max(np.abs(mine - cuda)) < 5e-7
+    t = (torch.rand(200000, generator=g) * math.pi - math.pi / 2).cuda()
+    t[:3] = torch.tensor([1e-6, -3e-4, 0.0])
+    s_mine = mpr.math_probe(2, t).double().cpu().numpy()
+    s_cuda = mpr.math_probe(3, t).double().cpu().numpy()
+    s_exact = np.sin(t.double().cpu().numpy())
+    rel = np.abs(s_mine - s_exact) / np.maximum(np.abs(s_exact), 1e-30)
+    assert np.max(rel[np.abs(s_exact) > 0]) < 3e-7
+    assert np.max(np.abs(s_mine - s_cuda)) < 3e-7
+
+
 # ------------------------------------------------------------- init
 
 @pytest.mark.parametrize("path", ["tiled", "plain"])
@@ -262,7 +282,8 @@ def test_energy_autograd_matches_finite_differences_and_oracle():
             b = p64.copy(); b[y, x] -= 1e-3
             fd = (oracle.energy(a, J=1.3) - oracle.energy(b, J=1.3)) / 2e-3 * w[k].item()
             assert abs(phi.grad[k, y, x].item() - fd) < 1e-5
-    dJ = sum(w[k].item() * oracle.energy(phi.detach()[k].cpu().numpy().astype(np.float64)) / 1.3
+    # dH/dJ = H / J = -sum cos(q dphi), the energy at J = 1
+    dJ = sum(w[k].item() * oracle.energy(phi.detach()[k].cpu().numpy().astype(np.float64), J=1.0)
              for k in range(2))
     assert abs(J.grad.item() - dJ) < 1e-4 * abs(dJ) + 1e-4
 
