@@ -230,6 +230,36 @@ mpr_status mpr_philox(int n, const uint32_t* ctr, const uint32_t* key, uint32_t*
 mpr_status mpr_math_probe(int fn, int n, const float* a, const float* b, float* out,
                           mpr_stream stream);
 
+/* ---- allocation-free entry point ------------------------------------------
+ *
+ * The sample specific energy of Eq. mpr-sse (with the sample extremes and
+ * pair counts) for callers that may not allocate device memory at all: code
+ * running where every byte of device memory belongs to another allocator (a
+ * plugin inside a framework with its own memory pool), real-time pipelines
+ * that forbid allocation once running, or hosts where an allocation would
+ * synchronise the device.  The paper has no counterpart of this entry point;
+ * it computes what mpr_init_grid() reports through mpr_get_image_info(), for
+ * up to MPR_NOALLOC_MAX_IMAGES images per call.
+ *
+ * Inputs and outputs are the caller's: z, gap as for mpr_init_grid (device,
+ * concatenated); e_s device [n_img] (nan when an image has fewer than two
+ * distinct sample values or no sample pair); n_sp, z_min, z_max device
+ * [n_img] or NULL.  Its temporary results go to a fixed array of about
+ * 0.5 MB that this library reserves in every GPU's memory when it is loaded
+ * (held until the process exits).  It calls no allocator.
+ *  - The first call on a device looks the array's device address up (a
+ *    cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device uses the same array: calls that may overlap on
+ *    the GPU (different streams, graph branches) race and must be ordered
+ *    by the caller.
+ * Asynchronous.  Errors: INVALID_ARG (n_img outside [1, 64], NULL pointers,
+ * bad sizes; the message names the limit), CUDA. */
+#define MPR_NOALLOC_MAX_IMAGES 64
+mpr_status mpr_sample_energy_noalloc(int n_img, const int* Lx, const int* Ly, const float* z,
+                                     const uint8_t* gap, double q, double J, double* e_s,
+                                     int64_t* n_sp, float* z_min, float* z_max,
+                                     mpr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

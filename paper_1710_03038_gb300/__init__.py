@@ -354,6 +354,32 @@ def math_probe(fn: int, a: torch.Tensor, b: torch.Tensor = None) -> torch.Tensor
     return out
 
 
+def sample_energy_noalloc(z, gap, q: float = 0.5, J: float = 1.0, out=None, stream=None):
+    """e_s, N_SP, z_min, z_max per image without any allocation inside the library.
+
+    z, gap: sequences of 2-D CUDA tensors (float32, uint8) or one concatenated
+    pair with ``shapes`` given through ``out``.  ``out`` may hold preallocated
+    device tensors dict(e_s=float64[n], n_sp=int64[n], zmin=float32[n],
+    zmax=float32[n]) so that the call itself allocates nothing.
+    """
+    zs, gs = _as_list(z), _as_list(gap)
+    shapes = [tuple(int(v) for v in g.shape) for g in gs]
+    n = len(shapes)
+    zf = zs[0] if n == 1 else torch.cat([t.reshape(-1) for t in zs])
+    gf = gs[0] if n == 1 else torch.cat([t.reshape(-1) for t in gs])
+    if out is None:
+        dev = zf.device
+        out = dict(e_s=torch.empty(n, dtype=torch.float64, device=dev),
+                   n_sp=torch.empty(n, dtype=torch.int64, device=dev),
+                   zmin=torch.empty(n, dtype=torch.float32, device=dev),
+                   zmax=torch.empty(n, dtype=torch.float32, device=dev))
+    call("mpr_sample_energy_noalloc", n, int_array([s[1] for s in shapes]),
+         int_array([s[0] for s in shapes]), _ptr(zf.contiguous()), _ptr(gf.contiguous()),
+         float(q), float(J), _ptr(out["e_s"]), _ptr(out["n_sp"]), _ptr(out["zmin"]),
+         _ptr(out["zmax"]), _stream_ptr(stream))
+    return out
+
+
 def philox(ctr: np.ndarray, key, reference: bool = False) -> np.ndarray:
     """Philox4x32-10 blocks computed on the GPU (reference=True: the CUDA toolkit's routine)."""
     c = torch.as_tensor(np.ascontiguousarray(ctr, dtype=np.uint32).view(np.int32), device="cuda")

@@ -31,6 +31,7 @@ EXPORTS = (
     "mpr_reset_accumulators", "mpr_get_state", "mpr_set_state", "mpr_get_chain_info",
     "mpr_set_chain_a", "mpr_get_sweep_index", "mpr_set_sweep_index", "mpr_destroy",
     "mpr_lattice_energy", "mpr_lattice_torque", "mpr_philox", "mpr_math_probe",
+    "mpr_sample_energy_noalloc",
 )
 
 
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
             "mpr_lattice_torque": (i, [i, ip, ip, vp, d, d, vp, vp, vp]),
             "mpr_philox": (i, [i, vp, u32p, vp, i, vp]),
             "mpr_math_probe": (i, [i, i, vp, vp, vp, vp]),
+            "mpr_sample_energy_noalloc": (i, [i, ip, ip, vp, vp, d, d, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)

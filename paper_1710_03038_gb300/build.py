@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmpr.so")
-SOURCES = ["mpr_api.cu", "mpr_tiled.cu", "mpr_plain.cu", "mpr_lattice.cu"]
+SOURCES = ["mpr_api.cu", "mpr_tiled.cu", "mpr_plain.cu", "mpr_lattice.cu", "mpr_noalloc.cu"]
 HEADERS = ["mpr_device.cuh", "mpr_internal.h", "mpr_async.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC",

@@ -147,6 +147,8 @@ int default_T_side(int Lx, int Ly, const mpr_T_opts& o) {
 
 }  // namespace
 
+mpr_status mpr::set_last_error(mpr_status s, const std::string& msg) { return fail(s, msg); }
+
 // ============================================================== context
 
 struct mpr_ctx {

@@ -86,6 +86,9 @@ struct SweepArgs {
     uint32_t img_tag;          // OR-ed into the image field of the counter (1 << 30: T lattices)
 };
 
+// Records the message returned by mpr_last_error() for this thread; returns s.
+mpr_status set_last_error(mpr_status s, const std::string& msg);
+
 // ---- launchers ------------------------------------------------------------
 cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tile_x, int tile_y,
                               cudaStream_t s);
