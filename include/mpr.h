@@ -75,7 +75,8 @@ typedef struct {
                                 as printed in Alg. 2 step 5.2                                   */
     int path;                /* mpr_path                                                       */
     int tile_x, tile_y;      /* tiled path tile shape; 0 = autotuned                          */
-    int chain_group;         /* tiled path: chains per thread block; 0 = autotuned            */
+    int chain_group;         /* tiled path: chains per thread block, even or >= n_chains;
+                                0 = automatic                                                  */
 } mpr_params;
 
 /* Options of the specific-energy-matching temperature estimate (Sec. 2.3). */

@@ -23,8 +23,9 @@
  *  - the sample specific energy averages over unordered sample-sample bonds
  *    (Eq. mpr-sse with N_SP the number of such pairs);
  *  - random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
- *    counter = (row << 16 | pair, sweep, chain, image | colour << 31), one
- *    call per two same-colour sites of a row; uniform = (w >> 8) * 2^-24.
+ *    counter = (row << 16 | x >> 1, sweep, chain >> 1, image | colour << 31),
+ *    one call per site and pair of realisations (words 0-1 for the even
+ *    realisation, 2-3 for the odd one); uniform = (w >> 8) * 2^-24.
  */
 #include <math.h>
 #include <stdint.h>
@@ -59,20 +60,22 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 
 static double u24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
 
-/* The two uniforms (u, r) of site (x, y) of colour `colour` at a given sweep.
- * In row y the sites of one colour have packed column k = x >> 1; sites k and
- * k ^ 1 share one Philox call, the even one taking words 0-1, the odd 2-3. */
+/* The two uniforms (u, r) of site (x, y) of colour `colour` in realisation
+ * `chain` at a given sweep.  In row y the sites of one colour have packed
+ * column k = x >> 1; one Philox call keyed by (row, k) serves that site in the
+ * two realisations 2m and 2m + 1: the even one takes words 0-1, the odd one
+ * words 2-3. */
 static void site_uniforms(uint64_t seed, uint32_t img, uint32_t chain, uint32_t sweep,
                           int x, int y, int colour, double* u, double* r)
 {
     uint32_t k = (uint32_t)x >> 1;
-    uint32_t ctr[4] = { ((uint32_t)y << 16) | (k >> 1), sweep, chain,
+    uint32_t ctr[4] = { ((uint32_t)y << 16) | k, sweep, chain >> 1,
                         img | ((uint32_t)colour << 31) };
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     uint32_t w[4];
     oracle_philox4x32_10(ctr, key, w);
-    if ((k & 1u) == 0) { *u = u24(w[0]); *r = u24(w[1]); }
-    else               { *u = u24(w[2]); *r = u24(w[3]); }
+    if ((chain & 1u) == 0) { *u = u24(w[0]); *r = u24(w[1]); }
+    else                   { *u = u24(w[2]); *r = u24(w[3]); }
 }
 
 static double mod_two_pi(double t) { return t - OR_TWO_PI * floor(t / OR_TWO_PI); }

@@ -262,7 +262,8 @@ class Context:
                     e_last=np.array(e[:]).reshape(shp))
 
     def set_chain_a(self, a, stream=None):
-        a = np.broadcast_to(np.asarray(a, dtype=np.float32), (self.n_img * self.chains,)).copy()
+        a = np.asarray(a, dtype=np.float32).reshape(-1)
+        a = np.broadcast_to(a, (self.n_img * self.chains,)).copy()
         call("mpr_set_chain_a", self._ctx, a.ctypes.data_as(C.POINTER(C.c_float)), _stream_ptr(stream))
 
     def sweep_index(self):

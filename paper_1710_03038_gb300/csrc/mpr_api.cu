@@ -102,9 +102,9 @@ Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_im
     L.img = take(sizeof(ImgDev) * g.n_img);
     L.ctl = take(sizeof(Control));
     L.ch_a = take(sizeof(float) * NC);
-    L.ch_cnt = take(sizeof(uint32_t) * NC);
+    L.ch_cnt = take(sizeof(uint32_t) * NC * kSpread);
     L.ch_last = take(sizeof(uint32_t) * NC);
-    L.ch_ecur = take(sizeof(double) * NC);
+    L.ch_ecur = take(sizeof(double) * NC * kSpread);
     L.ch_elast = take(sizeof(double) * NC);
     L.ch_esum = take(sizeof(double) * NC);
     L.ch_esum2 = take(sizeof(double) * NC);
@@ -179,6 +179,8 @@ struct mpr_ctx {
     // host mirrors
     std::vector<ImgDev> h_img;
     std::vector<long long> slots;
+    int gt[2] = {1, 1};           // tiled: per-warp table entries for the pass of colour c
+    int kload[2] = {1, 1};        // tiled: largest colour count of the pass's tiles / 32
     uint32_t sweep = 0, equil_index = 0;
     long long n_meas_done = 0;
     bool T_set = false;
@@ -344,11 +346,14 @@ __global__ void init_plain_kernel(const ImgDev* img, const float* samp, float* s
 }
 
 __global__ void init_chains_kernel(ChainDev ch, int nc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc * kSpread;
+         i += gridDim.x * blockDim.x) {
+        ch.acc_cnt[i] = 0;
+        ch.e_cur[i] = 0.0;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
         ch.a[i] = 1.0f;
-        ch.acc_cnt[i] = 0;
         ch.acc_last[i] = 0;
-        ch.e_cur[i] = 0.0;
         ch.e_last[i] = __longlong_as_double(0x7FF8000000000000LL);
         ch.e_sum[i] = 0.0;
         ch.e_sum2[i] = 0.0;
@@ -366,15 +371,20 @@ __global__ void end_sweep_kernel(const ImgDev* img, ChainDev ch, Control* ctl, i
     const int nc = n_img * n_chains;
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         const ImgDev& I = img[c / n_chains];
-        const uint32_t cnt = ch.acc_cnt[c];
+        uint32_t cnt = 0;
+        double e_gap = 0.0;
+        for (int k = 0; k < kSpread; ++k) {
+            cnt += ch.acc_cnt[c * kSpread + k];
+            ch.acc_cnt[c * kSpread + k] = 0;
+            e_gap += ch.e_cur[c * kSpread + k];
+            ch.e_cur[c * kSpread + k] = 0.0;
+        }
         ch.acc_last[c] = cnt;
-        ch.acc_cnt[c] = 0;
         if (equil && (double)cnt < A_targ * (double)I.n_gap)
             ch.a[c] = (float)(1.0 + (double)(i + 1) / k_a);
         if (record) {
-            const double e = (ch.e_cur[c] + (add_ess ? I.E_ss : 0.0)) / I.n_bonds;
+            const double e = (e_gap + (add_ess ? I.E_ss : 0.0)) / I.n_bonds;
             ch.e_last[c] = e;
-            ch.e_cur[c] = 0.0;
             if (stats) {
                 ch.e_sum[c] += e;
                 ch.e_sum2[c] += e * e;
@@ -568,9 +578,8 @@ void pick_tiles(const mpr_params& p, int n_img, const int* Lx, const int* Ly, in
     int mx = 0;
     for (int i = 0; i < n_img; ++i) { n += (long long)Lx[i] * Ly[i]; mx = std::max(mx, std::max(Lx[i], Ly[i])); }
     (void)n_chains;
-    if (mx <= 48) { tx = 32; ty = 16; }
-    else if (mx <= 96) { tx = 32; ty = 32; }
-    else { tx = 64; ty = 32; }
+    tx = 32;
+    ty = 16;
 }
 
 int pick_chain_group(const mpr_ctx* c) {
@@ -581,6 +590,7 @@ int pick_chain_group(const mpr_ctx* c) {
     const long long tiles = std::max(1, c->g.n_tiles);
     int cg = (int)std::min<long long>(64, std::max<long long>(1, tiles * c->g.n_chains / target));
     cg = std::min(cg, c->g.n_chains);
+    if (cg < c->g.n_chains) cg = std::max(2, cg & ~1);  // groups start at even chains
     return std::max(cg, 1);
 }
 
@@ -769,10 +779,20 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
                 }
             }
             c->slots[i] = off;
+            for (int t = g.tile0[i]; t < g.tile0[i] + g.ntiles[i]; ++t)
+                for (int col = 0; col < 2; ++col) {
+                    c->gt[col] = std::max(c->gt[col], h_counts[2 * t + (col ^ 1)] + g.halo_cap + 1);
+                    const int m = std::max(h_counts[2 * t], h_counts[2 * t + 1]);
+                    c->kload[col] = std::max(c->kload[col], (m + 31) / 32);
+                }
         } else {
             c->slots[i] = (long long)Lx[i] * Ly[i];
         }
     }
+    if (tiled && std::max(c->kload[0], c->kload[1]) > tiled_max_kload(tx, ty))
+        return fail(MPR_ERR_INVALID_ARG, "tile shape " + std::to_string(tx) + "x" +
+                                             std::to_string(ty) +
+                                             " cannot serve this gap density; use 32x16");
     c->L = make_layout(g, c->slots, sub_bytes, staging);
     if (c->L.total > ws_bytes)
         return fail(MPR_ERR_WORKSPACE, "workspace too small: need " + std::to_string(c->L.total) +
@@ -884,8 +904,10 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
     for (int k = 0; k < n; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
             a.colour = colour;
+            a.gt = c->gt[colour];
             a.flags = base | ((record && colour == 1) ? kEnergy : 0);
-            cudaError_t e = tiled ? launch_tiled_pass(a, c->g.n_tiles, c->g.tx, c->g.ty, s)
+            cudaError_t e = tiled ? launch_tiled_pass(a, c->g.n_tiles, c->g.tx, c->g.ty,
+                                                      c->kload[colour], s)
                                   : launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
         }
@@ -988,6 +1010,11 @@ mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly,
     mpr_ctx* c = new (std::nothrow) mpr_ctx();
     if (!c) return fail(MPR_ERR_INVALID_ARG, "out of host memory");
     c->p = *p;
+    if (p->chain_group > 0 && (p->chain_group & 1) && p->chain_group < n_chains) {
+        delete c;
+        return fail(MPR_ERR_INVALID_ARG, "chain_group must be even or cover every chain "
+                                         "(realisations 2m and 2m+1 share random numbers)");
+    }
     mpr_default_T_opts(&c->topt);
     if (T_opts) c->topt = *T_opts;
     if (c->topt.chains < 1 || c->topt.n_meas < 1 || c->topt.iters < 0 || c->topt.n_equil < 0 ||

@@ -48,21 +48,21 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* __res
 __device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
 
 // The random stream's counter for site (x, y) of colour `colour`: one Philox
-// call per two same-colour sites of a row (packed column k = x >> 1, pair
-// k >> 1).  sweep = 0xFFFFFFFF is the hot start.
+// call per site (packed column k = x >> 1 of its row) and per pair of
+// realisations (chain >> 1).  sweep = 0xFFFFFFFF is the hot start.
 __device__ __forceinline__ uint4 site_counter(int x, int y, int colour, uint32_t sweep,
                                               uint32_t chain, uint32_t img) {
-    const uint32_t k = (uint32_t)x >> 1;
-    return make_uint4(((uint32_t)y << 16) | (k >> 1), sweep, chain,
+    return make_uint4(((uint32_t)y << 16) | ((uint32_t)x >> 1), sweep, chain >> 1,
                       img | ((uint32_t)colour << 31));
 }
 
-// (u, r) of a site: words 0-1 for an even packed column, 2-3 for an odd one.
+// (u, r) of a site in realisation `chain`: words 0-1 for an even chain, 2-3
+// for an odd one.
 __device__ __forceinline__ void site_uniform_words(int x, int y, int colour, uint32_t sweep,
                                                    uint32_t chain, uint32_t img, uint2 key,
                                                    uint32_t& wu, uint32_t& wr) {
     const uint4 w = philox4x32_10(site_counter(x, y, colour, sweep, chain, img), key);
-    const bool odd = ((uint32_t)x >> 1) & 1u;
+    const bool odd = chain & 1u;
     wu = odd ? w.z : w.x;
     wr = odd ? w.w : w.y;
 }

@@ -45,7 +45,12 @@ struct Control {
     uint32_t pad;
 };
 
-// Per-chain device arrays (length n_img * n_chains, image-major).
+// Accept counts and energy partials of a chain are spread over kSpread
+// slots (indexed by thread block) to keep atomic traffic off a single address.
+constexpr int kSpread = 32;
+
+// Per-chain device arrays (length n_img * n_chains, image-major; acc_cnt and
+// e_cur are kSpread times longer).
 struct ChainDev {
     float* a;
     uint32_t* acc_cnt;    // accepted proposals of the sweep in progress
@@ -82,6 +87,7 @@ struct SweepArgs {
     int colour;
     int flags;
     int halo_cap;
+    int gt;                    // tiled: table entries per warp table for this pass
     int n_img;
     uint32_t img_tag;          // OR-ed into the image field of the counter (1 << 30: T lattices)
 };
@@ -91,9 +97,10 @@ mpr_status set_last_error(mpr_status s, const std::string& msg);
 
 // ---- launchers ------------------------------------------------------------
 cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tile_x, int tile_y,
-                              cudaStream_t s);
+                              int kload, cudaStream_t s);
 cudaError_t launch_plain_pass(const SweepArgs& a, int max_Lx, int max_Ly, cudaStream_t s);
 bool tiled_config_supported(int tile_x, int tile_y);
+int tiled_max_kload(int tile_x, int tile_y);  // largest per-lane site count a tile shape serves
 
 // tile-table construction (tiled path)
 cudaError_t launch_tile_count(const ImgDev* img, const TileDesc* tiles, int n_tiles,

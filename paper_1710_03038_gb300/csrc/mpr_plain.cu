@@ -41,13 +41,27 @@ plain_pass_kernel(SweepArgs a) {
         nb[1] = has[1] ? angle_of(P[i + I.Lx]) : 0.0f;
         nb[2] = has[2] ? angle_of(P[i - 1]) : 0.0f;
         nb[3] = has[3] ? angle_of(P[i + 1]) : 0.0f;
+        // local field: sample neighbours first, then gap neighbours, each in the
+        // order up, down, left, right (the tiled path sums in the same order)
+        bool fixed_nb[4];
+        fixed_nb[0] = has[0] && is_fixed(P[i - I.Lx]);
+        fixed_nb[1] = has[1] && is_fixed(P[i + I.Lx]);
+        fixed_nb[2] = has[2] && is_fixed(P[i - 1]);
+        fixed_nb[3] = has[3] && is_fixed(P[i + 1]);
+        float sn[4], cn[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) __sincosf(a.q * nb[j], &sn[j], &cn[j]);
         float C = 0.0f, S = 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float sj, cj;
-            __sincosf(a.q * nb[j], &sj, &cj);
-            C += has[j] ? cj : 0.0f;
-            S += has[j] ? sj : 0.0f;
+            C += fixed_nb[j] ? cn[j] : 0.0f;
+            S += fixed_nb[j] ? sn[j] : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool g = has[j] && !fixed_nb[j];
+            C += g ? cn[j] : 0.0f;
+            S += g ? sn[j] : 0.0f;
         }
         float phi_now = angle_of(v);
         if (!is_fixed(v)) {
@@ -73,12 +87,13 @@ plain_pass_kernel(SweepArgs a) {
                 e_site += has[j] ? -a.J * __cosf(a.q * (phi_now - nb[j])) : 0.0f;
         }
     }
-    const int ch_global = img * a.n_chains + chain;
+    const long long slot =
+        (long long)(img * a.n_chains + chain) * kSpread + ((blockIdx.x + blockIdx.y) & (kSpread - 1));
     n_acc = warp_sum(n_acc);
-    if ((threadIdx.x & 31) == 0 && n_acc) atomicAdd(a.ch.acc_cnt + ch_global, n_acc);
+    if ((threadIdx.x & 31) == 0 && n_acc) atomicAdd(a.ch.acc_cnt + slot, n_acc);
     if (a.flags & kEnergy) {
         const double e = warp_sum((double)e_site);
-        if ((threadIdx.x & 31) == 0 && e != 0.0) atomicAdd(a.ch.e_cur + ch_global, e);
+        if ((threadIdx.x & 31) == 0 && e != 0.0) atomicAdd(a.ch.e_cur + slot, e);
     }
 }
 

@@ -4,30 +4,30 @@
 // stored once per image (`samp`).  A realisation stores only its gap angles,
 // compactly: the image is cut into TX x TY tiles and the gap sites of one
 // tile and one colour form a contiguous segment of the image's slot space
-// (row-major inside the tile, padded to 4 slots = 16 bytes); the tile's red
-// and black segments are adjacent.  A chain's state is one float per slot.
+// (row-major inside the tile, padded to 4 slots).  A chain's state is one
+// float per slot.
 //
-// Work.  One thread block takes one tile and a group of chains.  Once per
-// launch it builds a shared-memory table of (cos q phi, sin q phi) for the
-// other-colour cells of the tile and its 1-cell ring, holding the sample
-// cells.  Then, chain after chain:
-//  - the tile's two segments of that chain arrive in a shared-memory stage
-//    buffer by one bulk asynchronous copy (issued two chains ahead, double
-//    buffered, completion tracked by an mbarrier);
-//  - the other-colour gap cells of the stage (and of the ring, whose values
-//    were prefetched into registers one chain ahead) are written into the
-//    table, and the own-colour angles are taken into registers;
-//  - every own-colour gap site gets the hybrid update of Alg. 1 from the
-//    table and its new angle is stored to global memory (coalesced).
-// Realisation sums stay in registers across the chain loop and reach global
-// memory once per tile.
+// Work.  One thread block takes one tile and a group of chains; each warp
+// takes pairs of realisations (2m, 2m + 1) of the group in turn.  Once per
+// launch the block prepares, for every own-colour gap site of the tile, the
+// constant part of its local field (the sines and cosines of its sample
+// neighbours, summed up, down, left, right) and four references into a
+// per-warp table of the other colour's gap cells (interior segment, then the
+// 1-cell ring, entry 0 holding zeros for neighbours that are not gaps).  For a
+// pair of realisations a warp
+//  - fills its two tables from the pair's other-colour gap angles (coalesced
+//    loads of the tile's segment, gathers for the ring),
+//  - updates every own-colour gap site of both realisations with Alg. 1, one
+//    Philox block serving the site in both (words 0-1 and 2-3), and stores
+//    the new angles (coalesced).
+// Warps synchronise only among their own lanes.  Realisation sums stay in
+// registers across a warp's pairs and reach global memory once per tile.
 //
 // Energy (black pass).  Every bond joins a red and a black site.  H is the
 // sample-sample part (constant, from the initialisation) plus the bonds of
 // black gap sites (-J R cos(theta - Psi) after their update) plus the bonds
 // between red gap sites and black sample sites (the red site's angle against
-// a per-tile constant field of its sample neighbours).
-#include "mpr_async.cuh"
+// the constant field of its sample neighbours).
 #include "mpr_device.cuh"
 #include "mpr_internal.h"
 
@@ -35,118 +35,86 @@ namespace mpr {
 
 namespace {
 
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NW>
 struct TiledCfg {
-    static constexpr int HW = TX / 2 + 1;          // other-colour cells per extended row
-    static constexpr int CSN = (TY + 2) * HW;      // cells of one table buffer
+    static constexpr int NT = NW * 32;
+    static constexpr int HK = (TX + TY + 31) / 32;  // ring cells per lane
+    static constexpr int EW = TX + 2;              // extended tile width
+    static constexpr int EXT = (TX + 2) * (TY + 2);
     static constexpr int NMAX = TX * TY / 2;       // sites of one colour in a tile
     static constexpr int HCAP = TX + TY;           // ring cells of one colour
-    static constexpr int KMAX = (NMAX + NT - 1) / NT;
-    static constexpr int KH = (HCAP + NT - 1) / NT;
-    static constexpr int SEG = TX * TY + 8;        // both padded segments of a tile
-    static constexpr int CGMAX = 64;               // chains per block
-    static constexpr size_t off_cs = 0;
-    static constexpr size_t off_stage = off_cs + sizeof(float2) * 2 * CSN;
-    static constexpr size_t off_csss = off_stage + sizeof(float) * 2 * SEG;
-    static constexpr size_t off_hslot = off_csss + sizeof(float2) * NMAX;
-    static constexpr size_t off_alpha = off_hslot + sizeof(int) * HCAP;
-    static constexpr size_t off_cnt = off_alpha + sizeof(float) * CGMAX;
-    static constexpr size_t off_e = off_cnt + sizeof(unsigned) * CGMAX;
-    static constexpr size_t off_bar = (off_e + sizeof(float) * CGMAX + 15) / 16 * 16;
-    static constexpr size_t off_c0 = off_bar + 16;
-    static constexpr size_t off_pos = off_c0 + sizeof(uint32_t) * NMAX;
-    static constexpr size_t smem_bytes = off_pos + sizeof(uint16_t) * (2 * NMAX + HCAP);
+    static constexpr int GT = NMAX + HCAP + 1;     // table entries (entry 0 = zeros)
+    static constexpr int KMAX = (NMAX + 31) / 32;
+    static constexpr size_t off_ref = 0;
+    static constexpr size_t off_cs = off_ref + sizeof(uint2) * NMAX;
+    static constexpr size_t off_csss = off_cs + sizeof(float2) * NMAX;
+    static constexpr size_t off_acc = off_csss + sizeof(float2) * NMAX;
+    static constexpr size_t off_c0 = off_acc + sizeof(float) * 2 * NMAX;
+    static constexpr size_t off_hslot = off_c0 + sizeof(uint32_t) * NMAX;
+    static constexpr size_t off_map = off_hslot + sizeof(int) * HCAP;
+    // per-warp tables last, sized at launch for the largest tile of the pass
+    static constexpr size_t off_tab = (off_map + sizeof(uint16_t) * EXT + 15) / 16 * 16;
+    static constexpr size_t smem_for(int gt) { return off_tab + sizeof(float2) * 2 * NW * gt; }
+    static constexpr size_t smem_max = smem_for(GT);
 };
 
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
+// K: gap sites per lane and realisation that one pass can meet (the largest
+// own or other-colour count of the pass's tiles, over 32, rounded up).
+template <int TX, int TY, int NW, int K>
+__global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))  // 64 registers: 32 warps per SM
 tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
-    using Cfg = TiledCfg<TX, TY, NT>;
-    constexpr int HW = Cfg::HW, CSN = Cfg::CSN, NMAX = Cfg::NMAX;
-    constexpr int KMAX = Cfg::KMAX, KH = Cfg::KH, SEG = Cfg::SEG;
+    using Cfg = TiledCfg<TX, TY, NW>;
+    constexpr int NT = Cfg::NT, EW = Cfg::EW, EXT = Cfg::EXT, NMAX = Cfg::NMAX;
+    constexpr int KMAX = K, HK = Cfg::HK;
+    static_assert(K * 32 <= NMAX || K == 1, "K larger than a tile's colour");
+    const int GT = a.gt;  // entries of one table (entry 0 = zeros)
     extern __shared__ __align__(16) unsigned char smem[];
-    float2* cs = reinterpret_cast<float2*>(smem + Cfg::off_cs);
-    float* stage = reinterpret_cast<float*>(smem + Cfg::off_stage);
+    uint2* own_ref = reinterpret_cast<uint2*>(smem + Cfg::off_ref);
+    float2* own_cs = reinterpret_cast<float2*>(smem + Cfg::off_cs);
     float2* csss = reinterpret_cast<float2*>(smem + Cfg::off_csss);
-    int* halo_slot = reinterpret_cast<int*>(smem + Cfg::off_hslot);
-    float* s_alpha = reinterpret_cast<float*>(smem + Cfg::off_alpha);
-    unsigned* s_cnt = reinterpret_cast<unsigned*>(smem + Cfg::off_cnt);
-    float* s_e = reinterpret_cast<float*>(smem + Cfg::off_e);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cfg::off_bar);
+    float2* tabs = reinterpret_cast<float2*>(smem + Cfg::off_tab);
+    float* acc_s = reinterpret_cast<float*>(smem + Cfg::off_acc);
     uint32_t* own_c0 = reinterpret_cast<uint32_t*>(smem + Cfg::off_c0);
-    uint16_t* own_nb = reinterpret_cast<uint16_t*>(smem + Cfg::off_pos);
-    uint16_t* oth_idx = own_nb + NMAX;
-    uint16_t* halo_idx = oth_idx + NMAX;
+    int* halo_slot = reinterpret_cast<int*>(smem + Cfg::off_hslot);
+    uint16_t* cellmap = reinterpret_cast<uint16_t*>(smem + Cfg::off_map);
 
     const int tid = threadIdx.x;
-    const int t = blockIdx.x;
-    // tile descriptor as scalars (runtime-indexed struct arrays would live in local memory)
-    const TileDesc* Tp = a.tiles + t;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const TileDesc* Tp = a.tiles + blockIdx.x;
     const int c = a.colour;
     const int oc = c ^ 1;
     const int n_own = Tp->cnt[c];
     if (n_own == 0) return;  // nothing of this colour to update in this tile
+    // tile descriptor as scalars (runtime-indexed struct arrays would live in local memory)
     const int t_img = Tp->img, t_x0 = Tp->x0, t_y0 = Tp->y0;
     const int off_own = Tp->off[c], off_oth = Tp->off[oc];
-    const int seg0 = Tp->off[0];
-    const int seg_len = Tp->off[1] + ((Tp->cnt[1] + 3) & ~3) - seg0;
+    const int n_oth = Tp->cnt[oc];
+    const int n_halo = Tp->halo_cnt[c];
     const ImgDev& I = a.img[t_img];
     const int r0 = blockIdx.y * a.chain_group;
     const int ng = min(a.chain_group, a.n_chains - r0);
-    const int n_oth = Tp->cnt[oc];
-    const int n_halo = Tp->halo_cnt[c];
     const uint32_t* spos = a.slot_pos + I.slot_off;
     const float* samp = a.samp + I.site_off;
     const bool energy = (a.flags & kEnergy) != 0;
     const bool accum = (a.flags & kAccumulate) != 0;
     const bool accum2 = (a.flags & kAccumulate2) != 0;
     const uint32_t sweep = a.ctl->sweep;
-    const uint32_t img_field = (uint32_t)t_img | a.img_tag;
+    const uint32_t c3 = (uint32_t)t_img | a.img_tag | ((uint32_t)c << 31);
     const UpdateConst uk{a.q, a.inv_q, a.two_pi_q, a.J};
     const float invT = I.invT;
-    // the tile's segments: [red | black], each padded to 4 slots
-    const uint32_t seg_bytes = (uint32_t)seg_len * 4u;
-    const int own_in = off_own - seg0;
-    const int oth_in = off_oth - seg0;
-    float* state0 = a.state + I.state_off + seg0;  // chain 0, start of the tile's segments
     const long long stride = I.stride;
+    const int spread = blockIdx.x & (kSpread - 1);
 
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    // -- prologue: sample cells of the table (both buffers) ------------------
-    for (int idx = tid; idx < CSN; idx += NT) {
-        const int yy = idx / HW;
-        const int kk = idx - yy * HW;
-        const int xx = 2 * kk + ((oc + yy) & 1);
-        float2 val = make_float2(0.0f, 0.0f);
-        const int X = t_x0 + xx - 1, Y = t_y0 + yy - 1;
-        if (xx < TX + 2 && X >= 0 && X < I.Lx && Y >= 0 && Y < I.Ly) {
-            const float v = samp[(long long)Y * I.Lx + X];
-            if (v >= 0.0f) __sincosf(a.q * v, &val.y, &val.x);
-        }
-        cs[idx] = val;
-        cs[CSN + idx] = val;
-    }
-    // own sites: table index of the upper neighbour with two flag bits (bit 14:
-    // extended column odd, so the left neighbour shares the upper one's packed
-    // column; bit 15: odd packed column, so the site takes Philox words 2-3) and
-    // the first counter word (row << 16 | pair)
-    for (int j = tid; j < n_own; j += NT) {
-        const uint32_t p = spos[off_own + j];
-        const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
-        const int xx = X - t_x0 + 1, yy = Y - t_y0 + 1;
-        own_nb[j] = (uint16_t)(((yy - 1) * HW + (xx >> 1)) | ((xx & 1) << 14) |
-                               ((((uint32_t)X >> 1) & 1u) << 15));
-        own_c0[j] = ((uint32_t)Y << 16) | ((uint32_t)X >> 2);
-    }
+    // -- prologue ---------------------------------------------------------------
+    for (int i = tid; i < EXT; i += NT) cellmap[i] = 0;
+    for (int i = tid; i < 2 * NMAX; i += NT) acc_s[i] = 0.0f;
+    for (int i = tid; i < 2 * NW; i += NT) tabs[i * GT] = make_float2(0.0f, 0.0f);
+    __syncthreads();
     for (int j = tid; j < n_oth; j += NT) {
         const uint32_t p = spos[off_oth + j];
         const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
-        const int xx = X - t_x0 + 1, yy = Y - t_y0 + 1;
-        oth_idx[j] = (uint16_t)(yy * HW + (xx >> 1));
+        cellmap[(Y - t_y0 + 1) * EW + (X - t_x0 + 1)] = (uint16_t)(1 + j);
         if (energy) {
             // field of the sample neighbours of this other-colour gap site
             float2 f = make_float2(0.0f, 0.0f);
@@ -166,161 +134,188 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
             csss[j] = f;
         }
     }
-    const int2* hl = a.halo + ((long long)t * 2 + c) * a.halo_cap;
-    for (int j = tid; j < n_halo; j += NT) {
-        const int2 h = hl[j];
-        halo_slot[j] = h.x;
-        halo_idx[j] = (uint16_t)h.y;
-    }
-    for (int j = tid; j < ng; j += NT) {
-        const int chg = t_img * a.n_chains + r0 + j;
-        s_alpha[j] = (a.flags & kAlphaOne) ? kTwoPi : kTwoPi / a.ch.a[chg];
-        s_cnt[j] = 0u;
-        s_e[j] = 0.0f;
+    {
+        const int2* hl = a.halo + ((long long)blockIdx.x * 2 + c) * a.halo_cap;
+        for (int k = tid; k < n_halo; k += NT) {
+            const int2 h = hl[k];
+            halo_slot[k] = h.x;
+            cellmap[h.y] = (uint16_t)(1 + n_oth + k);
+        }
     }
     __syncthreads();
-    if (tid == 0) {
-        for (int q = 0; q < 2 && q < ng; ++q) {
-            mbar_arrive_expect_tx(&bar[q], seg_bytes);
-            bulk_copy_g2s(stage + q * SEG, state0 + (long long)(r0 + q) * stride, seg_bytes, &bar[q]);
-        }
-    }
-    // ring values of the first chain
-    float hv[KH];
-    {
-        const float* st = a.state + I.state_off + (long long)r0 * stride;
+    for (int j = tid; j < n_own; j += NT) {
+        const uint32_t p = spos[off_own + j];
+        const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
+        const int xx = X - t_x0 + 1, yy = Y - t_y0 + 1;
+        float2 f = make_float2(0.0f, 0.0f);
+        uint32_t ref[4];
 #pragma unroll
-        for (int kh = 0; kh < KH; ++kh) {
-            const int j = tid + kh * NT;
-            hv[kh] = j < n_halo ? st[halo_slot[j]] : 0.0f;
+        for (int m = 0; m < 4; ++m) {  // up, down, left, right
+            const int dx = m < 2 ? 0 : 2 * m - 5;
+            const int dy = m < 2 ? 2 * m - 1 : 0;
+            const int nx = X + dx, ny = Y + dy;
+            ref[m] = 0u;
+            if (nx < 0 || nx >= I.Lx || ny < 0 || ny >= I.Ly) continue;
+            const float v = samp[(long long)ny * I.Lx + nx];
+            if (v >= 0.0f) {
+                float s, cc;
+                __sincosf(a.q * v, &s, &cc);
+                f.x += cc;
+                f.y += s;
+            } else {
+                ref[m] = cellmap[(yy + dy) * EW + (xx + dx)];
+            }
         }
+        own_ref[j] = make_uint2(ref[0] | (ref[1] << 16), ref[2] | (ref[3] << 16));
+        own_cs[j] = f;
+        own_c0[j] = ((uint32_t)Y << 16) | ((uint32_t)X >> 1);
     }
+    __syncthreads();
 
+    // -- chain pairs ------------------------------------------------------------
+    float2* tab0 = tabs + (2 * warp) * GT;
+    float2* tab1 = tab0 + GT;
     float accv[KMAX];
     float accq[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) { accv[k] = 0.0f; accq[k] = 0.0f; }
-
-    for (int rr = 0; rr < ng; ++rr) {
-        const int buf = rr & 1;
-        const int chain = r0 + rr;
-        float* st = a.state + I.state_off + (long long)chain * stride;
-        float2* CS = cs + buf * CSN;
-        const float* stg = stage + buf * SEG;
-        float e_loc = 0.0f;
-        // ring values of the next chain, in flight during this one
-        float hn[KH];
-        if (rr + 1 < ng) {
-            const float* stn = st + stride;
-#pragma unroll
-            for (int kh = 0; kh < KH; ++kh) {
-                const int j = tid + kh * NT;
-                hn[kh] = j < n_halo ? stn[halo_slot[j]] : 0.0f;
-            }
-        }
-        const bool ok = mbar_wait_bounded(&bar[buf], (uint32_t)(rr >> 1) & 1u);
-        if (__syncthreads_or(!ok)) {
-            // a copy did not complete in time: record it, give the copies still in
-            // flight a bounded chance to land, and leave
-            if (tid == 0) {
-                atomicOr(&a.ctl->status, 1u);
-                mbar_wait_bounded(&bar[buf], (uint32_t)(rr >> 1) & 1u);
-                if (rr + 1 < ng) mbar_wait_bounded(&bar[buf ^ 1], (uint32_t)((rr + 1) >> 1) & 1u);
-            }
-            __syncthreads();
-            return;
-        }
-        // other-colour gap cells of this chain
-        for (int j = tid; j < n_oth; j += NT) {
-            const float v = stg[oth_in + j];
-            float s, cc;
-            __sincosf(a.q * v, &s, &cc);
-            CS[oth_idx[j]] = make_float2(cc, s);
-            if (energy) {
-                const float2 f = csss[j];
-                e_loc -= a.J * fmaf(f.x, cc, f.y * s);
-            }
-        }
-#pragma unroll
-        for (int kh = 0; kh < KH; ++kh) {
-            const int j = tid + kh * NT;
-            if (j < n_halo) {
-                float s, cc;
-                __sincosf(a.q * hv[kh], &s, &cc);
-                CS[halo_idx[j]] = make_float2(cc, s);
-            }
-        }
-        float ov[KMAX];
+    const int n_pairs = (ng + 1) >> 1;
+    for (int pi = warp; pi < n_pairs; pi += NW) {
+        const int ch0 = r0 + 2 * pi;
+        const bool has1 = 2 * pi + 1 < ng;
+        const float* st0 = a.state + I.state_off + (long long)ch0 * stride;
+        const float* st1 = st0 + stride;
+        // every load of this pair first (one memory latency per pair)
+        float oth0[KMAX], oth1[KMAX], own0[KMAX], own1[KMAX], hal0[HK], hal1[HK];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const int j = tid + k * NT;
-            ov[k] = j < n_own ? stg[own_in + j] : 0.0f;
+            const int j = lane + k * 32;
+            oth0[k] = j < n_oth ? st0[off_oth + j] : 0.0f;
+            oth1[k] = (has1 && j < n_oth) ? st1[off_oth + j] : 0.0f;
+            own0[k] = j < n_own ? st0[off_own + j] : 0.0f;
+            own1[k] = (has1 && j < n_own) ? st1[off_own + j] : 0.0f;
         }
-        __syncthreads();
-        // the stage buffer is free again: fetch the chain after next into it
-        if (tid == 0 && rr + 2 < ng) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[buf], seg_bytes);
-            bulk_copy_g2s(stage + buf * SEG, state0 + (long long)(chain + 2) * stride, seg_bytes,
-                          &bar[buf]);
+#pragma unroll
+        for (int k = 0; k < HK; ++k) {
+            const int j = lane + k * 32;
+            const int hs = j < n_halo ? halo_slot[j] : 0;
+            hal0[k] = j < n_halo ? st0[hs] : 0.0f;
+            hal1[k] = (has1 && j < n_halo) ? st1[hs] : 0.0f;
         }
-        const float alpha = s_alpha[rr];
-        unsigned cnt = 0;
+        float e0 = 0.0f, e1 = 0.0f;
+        // other-colour gap cells of the two realisations (straight-line per
+        // iteration: only the side effects are guarded, so independent work
+        // of both realisations can interleave)
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const int j = tid + k * NT;
-            if (j < n_own) {
-                const uint32_t nb = own_nb[j];
-                const int up = (int)(nb & 0x0FFFu);
-                const int left = up + HW - 1 + (int)((nb >> 14) & 1u);
-                const float2 fu = CS[up];
-                const float2 fd = CS[up + 2 * HW];
-                const float2 fl = CS[left];
-                const float2 fr = CS[left + 1];
-                const float C = ((fu.x + fd.x) + fl.x) + fr.x;
-                const float S = ((fu.y + fd.y) + fl.y) + fr.y;
-                const uint4 w = philox4x32_10_rk(
-                    make_uint4(own_c0[j], sweep, (uint32_t)chain, img_field | ((uint32_t)c << 31)),
-                    a.rk);
-                const bool odd = (nb >> 15) != 0;
-                const uint32_t wu = odd ? w.z : w.x;
-                const uint32_t wr = odd ? w.w : w.y;
-                const UpdateOut o = hybrid_update(ov[k], C, S, wu, wr, uk, alpha, invT);
-                st[off_own + j] = o.phi;
-                cnt += o.accepted;
-                if (energy) e_loc += site_energy_after(o, a.J);
-                if (accum) {
-                    accv[k] += o.phi;
-                    if (accum2) accq[k] = fmaf(o.phi, o.phi, accq[k]);
+            if (k * 32 >= n_oth) break;
+            const int j = lane + k * 32;
+            const bool act = j < n_oth;
+            float s0, c0, s1, c1;
+            __sincosf(a.q * oth0[k], &s0, &c0);
+            __sincosf(a.q * oth1[k], &s1, &c1);
+            if (act) {
+                tab0[1 + j] = make_float2(c0, s0);
+                if (has1) tab1[1 + j] = make_float2(c1, s1);
+                if (energy) {
+                    const float2 f = csss[j];
+                    e0 -= a.J * fmaf(f.x, c0, f.y * s0);
+                    if (has1) e1 -= a.J * fmaf(f.x, c1, f.y * s1);
                 }
             }
         }
-        cnt = warp_sum(cnt);
-        if ((tid & 31) == 0 && cnt) atomicAdd(s_cnt + rr, cnt);
-        if (energy) {
-            e_loc = warp_sum(e_loc);
-            if ((tid & 31) == 0) atomicAdd(s_e + rr, e_loc);
-        }
-        if (rr + 1 < ng) {
 #pragma unroll
-            for (int kh = 0; kh < KH; ++kh) hv[kh] = hn[kh];
+        for (int k = 0; k < HK; ++k) {
+            if (k * 32 >= n_halo) break;
+            const int j = lane + k * 32;
+            float s0, c0, s1, c1;
+            __sincosf(a.q * hal0[k], &s0, &c0);
+            __sincosf(a.q * hal1[k], &s1, &c1);
+            if (j < n_halo) {
+                tab0[1 + n_oth + j] = make_float2(c0, s0);
+                if (has1) tab1[1 + n_oth + j] = make_float2(c1, s1);
+            }
         }
-    }
-    __syncthreads();
-    for (int j = tid; j < ng; j += NT) {
-        const int chg = t_img * a.n_chains + r0 + j;
-        if (s_cnt[j]) atomicAdd(a.ch.acc_cnt + chg, s_cnt[j]);
-        if (energy) atomicAdd(a.ch.e_cur + chg, (double)s_e[j]);
-    }
-    if (accum) {
-        double* acc1 = a.acc1 + I.slot_off + off_own;
-        double* acc2 = a.acc2 + I.slot_off + off_own;
+        __syncwarp();
+        const float alpha0 = (a.flags & kAlphaOne) ? kTwoPi
+                                                    : kTwoPi / a.ch.a[t_img * a.n_chains + ch0];
+        const float alpha1 = (a.flags & kAlphaOne) || !has1
+                                 ? kTwoPi
+                                 : kTwoPi / a.ch.a[t_img * a.n_chains + ch0 + 1];
+        float* out0 = a.state + I.state_off + (long long)ch0 * stride + off_own;
+        float* out1 = out0 + stride;
+        unsigned cnt0 = 0, cnt1 = 0;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            const int j = tid + k * NT;
+            if (k * 32 >= n_own) break;
+            const int j = lane + k * 32;
+            const bool act = j < n_own;
+            const int jj = act ? j : 0;  // idle lanes recompute slot 0 and store nothing
+            const uint2 rf = own_ref[jj];
+            const float2 fs = own_cs[jj];
+            const uint4 w = philox4x32_10_rk(make_uint4(own_c0[jj], sweep, (uint32_t)ch0 >> 1, c3),
+                                             a.rk);
+            const int ru = rf.x & 0xFFFFu, rd = rf.x >> 16, rl = rf.y & 0xFFFFu, rr = rf.y >> 16;
+            const float2 gu0 = tab0[ru], gd0 = tab0[rd], gl0 = tab0[rl], gr0 = tab0[rr];
+            const float2 gu1 = tab1[ru], gd1 = tab1[rd], gl1 = tab1[rl], gr1 = tab1[rr];
+            const float C0 = (((fs.x + gu0.x) + gd0.x) + gl0.x) + gr0.x;
+            const float S0 = (((fs.y + gu0.y) + gd0.y) + gl0.y) + gr0.y;
+            const float C1 = (((fs.x + gu1.x) + gd1.x) + gl1.x) + gr1.x;
+            const float S1 = (((fs.y + gu1.y) + gd1.y) + gl1.y) + gr1.y;
+            const UpdateOut o0 = hybrid_update(own0[k], C0, S0, w.x, w.y, uk, alpha0, invT);
+            const UpdateOut o1 = hybrid_update(own1[k], C1, S1, w.z, w.w, uk, alpha1, invT);
+            const bool act1 = act && has1;
+            if (act) out0[j] = o0.phi;
+            if (act1) out1[j] = o1.phi;
+            cnt0 += (act && o0.accepted) ? 1u : 0u;
+            cnt1 += (act1 && o1.accepted) ? 1u : 0u;
+            if (energy) {
+                if (act) e0 += site_energy_after(o0, a.J);
+                if (act1) e1 += site_energy_after(o1, a.J);
+            }
+            if (accum) {
+                const float p0 = act ? o0.phi : 0.0f, p1 = act1 ? o1.phi : 0.0f;
+                accv[k] += p0 + p1;
+                if (accum2) accq[k] = fmaf(p0, p0, fmaf(p1, p1, accq[k]));
+            }
+        }
+        cnt0 = warp_sum(cnt0);
+        cnt1 = warp_sum(cnt1);
+        if (energy) {
+            e0 = warp_sum(e0);
+            e1 = warp_sum(e1);
+        }
+        if (lane == 0) {
+            const long long b0 = (long long)(t_img * a.n_chains + ch0) * kSpread + spread;
+            if (cnt0) atomicAdd(a.ch.acc_cnt + b0, cnt0);
+            if (energy) atomicAdd(a.ch.e_cur + b0, (double)e0);
+            if (has1) {
+                if (cnt1) atomicAdd(a.ch.acc_cnt + b0 + kSpread, cnt1);
+                if (energy) atomicAdd(a.ch.e_cur + b0 + kSpread, (double)e1);
+            }
+        }
+        __syncwarp();  // the tables are refilled by the next pair
+    }
+    if (accum) {
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int j = lane + k * 32;
             if (j < n_own) {
-                atomicAdd(acc1 + j, (double)accv[k]);
-                if (accum2) atomicAdd(acc2 + j, (double)accq[k]);
+                atomicAdd(acc_s + j, accv[k]);
+                if (accum2) atomicAdd(acc_s + NMAX + j, accq[k]);
+            }
+        }
+        __syncthreads();
+        const bool shared_slots = gridDim.y > 1;
+        double* acc1 = a.acc1 + I.slot_off + off_own;
+        double* acc2 = a.acc2 + I.slot_off + off_own;
+        for (int j = tid; j < n_own; j += NT) {
+            if (shared_slots) {
+                atomicAdd(acc1 + j, (double)acc_s[j]);
+                if (accum2) atomicAdd(acc2 + j, (double)acc_s[NMAX + j]);
+            } else {
+                acc1[j] += (double)acc_s[j];
+                if (accum2) acc2[j] += (double)acc_s[NMAX + j];
             }
         }
     }
@@ -405,7 +400,6 @@ __global__ void tile_halo_kernel(const ImgDev* img, TileDesc* tiles, const int* 
     const ImgDev& I = img[T.img];
     if (threadIdx.x < 2) n[threadIdx.x] = 0;
     __syncthreads();
-    const int hw = tx / 2 + 1;
     const int ring = 2 * tx + 2 * ty;
     for (int i = threadIdx.x; i < ring; i += blockDim.x) {
         int xx, yy;
@@ -419,7 +413,7 @@ __global__ void tile_halo_kernel(const ImgDev* img, TileDesc* tiles, const int* 
         if (slot < 0) continue;
         const int pass = ((xx + yy) & 1) ^ 1;  // the colour whose update reads this cell
         const int k = atomicAdd(&n[pass], 1);
-        if (k < cap) halo[((long long)t * 2 + pass) * cap + k] = make_int2(slot, yy * hw + (xx >> 1));
+        if (k < cap) halo[((long long)t * 2 + pass) * cap + k] = make_int2(slot, yy * (tx + 2) + xx);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -428,37 +422,53 @@ __global__ void tile_halo_kernel(const ImgDev* img, TileDesc* tiles, const int* 
     }
 }
 
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NW, int K>
 cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s) {
-    using Cfg = TiledCfg<TX, TY, NT>;
+    using Cfg = TiledCfg<TX, TY, NW>;
+    static_assert(Cfg::smem_max <= 227 * 1024, "shared memory");
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tiled_pass_kernel<TX, TY, NT>,
+        cudaError_t e = cudaFuncSetAttribute(tiled_pass_kernel<TX, TY, NW, K>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Cfg::smem_bytes);
+                                             (int)Cfg::smem_max);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (a.chain_group > Cfg::CGMAX) return cudaErrorInvalidValue;
+    if (a.gt < 1 || a.gt > Cfg::GT) return cudaErrorInvalidValue;
     dim3 grid(n_tiles, (a.n_chains + a.chain_group - 1) / a.chain_group);
-    tiled_pass_kernel<TX, TY, NT><<<grid, NT, Cfg::smem_bytes, s>>>(a);
+    tiled_pass_kernel<TX, TY, NW, K><<<grid, Cfg::NT, Cfg::smem_for(a.gt), s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tiled_config_supported(int tx, int ty) {
-    static_assert(TiledCfg<64, 64, 256>::smem_bytes < 227 * 1024, "shared memory");
-    return (tx == 64 && ty == 64) || (tx == 64 && ty == 32) || (tx == 32 && ty == 32) ||
-           (tx == 128 && ty == 32) || (tx == 32 && ty == 16);
+    return (tx == 32 && ty == 16) || (tx == 16 && ty == 16) || (tx == 32 && ty == 32);
 }
 
-cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, cudaStream_t s) {
-    if (tx == 64 && ty == 64) return launch_cfg<64, 64, 256>(a, n_tiles, s);
-    if (tx == 64 && ty == 32) return launch_cfg<64, 32, 256>(a, n_tiles, s);
-    if (tx == 32 && ty == 32) return launch_cfg<32, 32, 128>(a, n_tiles, s);
-    if (tx == 128 && ty == 32) return launch_cfg<128, 32, 256>(a, n_tiles, s);
-    if (tx == 32 && ty == 16) return launch_cfg<32, 16, 128>(a, n_tiles, s);
+int tiled_max_kload(int tx, int ty) {
+    return tx * ty / 64;  // every site of one colour
+}
+
+// kload = largest gap count of one colour over the pass's tiles, over 32, rounded up.
+cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, int kload,
+                              cudaStream_t s) {
+    if (a.chain_group % 2 != 0 && a.chain_group < a.n_chains) return cudaErrorInvalidValue;
+    if (tx == 32 && ty == 16) {
+        if (kload <= 3) return launch_cfg<32, 16, 8, 3>(a, n_tiles, s);
+        if (kload <= 4) return launch_cfg<32, 16, 8, 4>(a, n_tiles, s);
+        if (kload <= 5) return launch_cfg<32, 16, 8, 5>(a, n_tiles, s);
+        if (kload <= 6) return launch_cfg<32, 16, 8, 6>(a, n_tiles, s);
+        return launch_cfg<32, 16, 8, 8>(a, n_tiles, s);
+    }
+    if (tx == 16 && ty == 16) {
+        if (kload <= 2) return launch_cfg<16, 16, 4, 2>(a, n_tiles, s);
+        return launch_cfg<16, 16, 4, 4>(a, n_tiles, s);
+    }
+    if (tx == 32 && ty == 32) {
+        if (kload <= 8) return launch_cfg<32, 32, 8, 8>(a, n_tiles, s);
+        return launch_cfg<32, 32, 8, 16>(a, n_tiles, s);
+    }
     return cudaErrorInvalidValue;
 }
 

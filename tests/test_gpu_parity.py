@@ -210,7 +210,7 @@ def test_tiled_and_plain_paths_agree_bitwise():
         assert np.allclose(a, b, rtol=1e-6, atol=1e-5)
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 32), (64, 64), (128, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (32, 32)])
 def test_tile_shapes_and_chain_groups_agree_bitwise(tile):
     zs, gs = ragged_images()
     R = 5
@@ -218,7 +218,7 @@ def test_tile_shapes_and_chain_groups_agree_bitwise(tile):
     ref.set_T([0.2, 0.2, 0.1, 0.4])
     ref.sweep(3, "equil")
     want = [s.cpu().numpy() for s in ref.get_state()]
-    for cg in (1, 2, 5):
+    for cg in (2, 4, 5):
         ctx = make_ctx(zs, gs, R, "tiled", tile=tile, chain_group=cg)
         ctx.set_T([0.2, 0.2, 0.1, 0.4])
         ctx.sweep(3, "equil")
@@ -235,10 +235,12 @@ def test_determinism_same_state_same_result():
     ctx.sweep(2, "equil")
     s0 = [s.clone() for s in ctx.get_state()]
     idx = ctx.sweep_index()
+    a0 = ctx.chain_info()["a"]
     ctx.sweep(1, "equil")
     r1 = [s.clone() for s in ctx.get_state()]
     ctx.set_state(s0)
     ctx.set_sweep_index(*idx)
+    ctx.set_chain_a(a0)
     ctx.sweep(1, "equil")
     r2 = ctx.get_state()
     for a, b in zip(r1, r2):
