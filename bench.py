@@ -275,7 +275,10 @@ def run_gpu(args):
     # kernel launches of one step: 3 per sweep (two colour passes + bookkeeping) for the
     # main chains and for the temperature lattices, plus the fixed init/predict kernels
     t_sweeps = topts.iters * (topts.n_equil + topts.n_meas) + topts.n_equil
-    line["gpu_launches"] = args.steps * (3 * (ne + nm) + 3 * t_sweeps + topts.iters + 1 + 14)
+    # per step: 3 launches per sweep (two colour passes + bookkeeping) for the
+    # realisations and for the temperature lattices, the Newton steps and the
+    # init / predict kernels of both contexts
+    line["gpu_launches"] = args.steps * (3 * (ne + nm) + 3 * t_sweeps + topts.iters + 1 + 16)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -82,10 +82,11 @@ typedef struct {
 /* Options of the specific-energy-matching temperature estimate (Sec. 2.3). */
 typedef struct {
     int L;                 /* side of the unconditional lattice for e(T); 0: min(256, image side) */
-    int chains;            /* independent unconditional chains per image; 4                      */
-    int n_equil;           /* sweeps after each temperature change; 60                           */
-    int n_meas;            /* sweeps averaged for <e> and Var(e) per iteration; 120              */
-    int iters;             /* Newton iterations; 6                                               */
+    int chains;            /* independent unconditional chains per image; 16                     */
+    int n_equil;           /* sweeps after each temperature change (twice that from the hot
+                              start); 40                                                         */
+    int n_meas;            /* sweeps averaged for <e> and Var(e) per iteration; 40               */
+    int iters;             /* Newton iterations; 4                                               */
     double T_lo, T_hi;     /* safeguarding bracket; 1e-5, 20                                      */
 } mpr_T_opts;
 

@@ -58,10 +58,10 @@ class Params:
 class TOpts:
     """Options of the temperature estimate (unconditional lattice side, chains, sweeps)."""
     L: int = 0
-    chains: int = 4
-    n_equil: int = 60
-    n_meas: int = 120
-    iters: int = 6
+    chains: int = 16
+    n_equil: int = 40
+    n_meas: int = 40
+    iters: int = 4
     T_lo: float = 1e-5
     T_hi: float = 20.0
 

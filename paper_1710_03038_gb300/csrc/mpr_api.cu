@@ -363,22 +363,24 @@ __global__ void init_chains_kernel(ChainDev ch, int nc) {
 // ======================================================= sweep kernels
 
 // Bookkeeping after every sweep: acceptance -> a (Alg. 2 step 4.2), energy
-// record (step 4.3), counters.  One block.
+// record (step 4.3), counters.  One block; one warp per chain at a time sums
+// the chain's kSpread partial slots.
 __global__ void end_sweep_kernel(const ImgDev* img, ChainDev ch, Control* ctl, int n_img,
                                  int n_chains, int equil, int record, int stats, int add_ess,
                                  double A_targ, double k_a) {
+    static_assert(kSpread == 32, "one lane per spread slot");
     const uint32_t i = ctl->equil_index;
     const int nc = n_img * n_chains;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int c = threadIdx.x >> 5; c < nc; c += blockDim.x >> 5) {
         const ImgDev& I = img[c / n_chains];
-        uint32_t cnt = 0;
-        double e_gap = 0.0;
-        for (int k = 0; k < kSpread; ++k) {
-            cnt += ch.acc_cnt[c * kSpread + k];
-            ch.acc_cnt[c * kSpread + k] = 0;
-            e_gap += ch.e_cur[c * kSpread + k];
-            ch.e_cur[c * kSpread + k] = 0.0;
-        }
+        uint32_t cnt = ch.acc_cnt[c * kSpread + lane];
+        double e_gap = ch.e_cur[c * kSpread + lane];
+        ch.acc_cnt[c * kSpread + lane] = 0;
+        ch.e_cur[c * kSpread + lane] = 0.0;
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        e_gap = warp_sum(e_gap);
+        if (lane != 0) continue;
         ch.acc_last[c] = cnt;
         if (equil && (double)cnt < A_targ * (double)I.n_gap)
             ch.a[c] = (float)(1.0 + (double)(i + 1) / k_a);
@@ -911,7 +913,7 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
                                   : launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
         }
-        end_sweep_kernel<<<1, 256, 0, s>>>(c->d_img, c->ch, c->d_ctl, c->g.n_img, c->g.n_chains,
+        end_sweep_kernel<<<1, 1024, 0, s>>>(c->d_img, c->ch, c->d_ctl, c->g.n_img, c->g.n_chains,
                                            equil ? 1 : 0, record ? 1 : 0, stats ? 1 : 0,
                                            tiled ? 1 : 0, c->p.A_targ, c->p.k_a);
         MPR_CUDA(cudaGetLastError());
@@ -975,10 +977,10 @@ mpr_status mpr_default_params(mpr_params* p) {
 mpr_status mpr_default_T_opts(mpr_T_opts* o) {
     if (!o) return fail(MPR_ERR_INVALID_ARG, "NULL");
     o->L = 0;
-    o->chains = 4;
-    o->n_equil = 60;
-    o->n_meas = 120;
-    o->iters = 6;
+    o->chains = 16;
+    o->n_equil = 40;
+    o->n_meas = 40;
+    o->iters = 4;
     o->T_lo = 1e-5;
     o->T_hi = 20.0;
     return MPR_OK;

@@ -85,7 +85,9 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const int c = a.colour;
     const int oc = c ^ 1;
     const int n_own = Tp->cnt[c];
-    if (n_own == 0) return;  // nothing of this colour to update in this tile
+    const bool energy = (a.flags & kEnergy) != 0;
+    // nothing to update and no red-gap / black-sample bond energy to add
+    if (n_own == 0 && !(energy && Tp->cnt[oc] > 0)) return;
     // tile descriptor as scalars (runtime-indexed struct arrays would live in local memory)
     const int t_img = Tp->img, t_x0 = Tp->x0, t_y0 = Tp->y0;
     const int off_own = Tp->off[c], off_oth = Tp->off[oc];
@@ -96,7 +98,6 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const int ng = min(a.chain_group, a.n_chains - r0);
     const uint32_t* spos = a.slot_pos + I.slot_off;
     const float* samp = a.samp + I.site_off;
-    const bool energy = (a.flags & kEnergy) != 0;
     const bool accum = (a.flags & kAccumulate) != 0;
     const bool accum2 = (a.flags & kAccumulate2) != 0;
     const uint32_t sweep = a.ctl->sweep;
