@@ -279,6 +279,29 @@ def run_gpu(args):
     # realisations and for the temperature lattices, the Newton steps and the
     # init / predict kernels of both contexts
     line["gpu_launches"] = args.steps * (3 * (ne + nm) + 3 * t_sweeps + topts.iters + 1 + 16)
+    if not args.no_plain:
+        # the plain single-image path on the same job (one warm-up, one timed step)
+        plain = mpr.Params(seed=12345 + rank, path="plain")
+        pctx = mpr.Context([z_d], [g_d], chains=R, params=plain, topts=topts, device=dev)
+        pctx.close()
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        ctx_p = mpr.Context([z_d], [g_d], chains=R, params=plain, topts=topts, device=dev)
+        if args.T is None:
+            ctx_p.estimate_T_async()
+        else:
+            ctx_p.set_T([args.T])
+        ctx_p.sweep(ne, "equil")
+        ctx_p.sweep(nm, "measure")
+        ctx_p.predict()
+        q1.record(stream)
+        torch.cuda.synchronize()
+        ctx_p.close()
+        plain_value = units_step / (q0.elapsed_time(q1) / 1e3)
+        line["plain_path"] = {"value": plain_value, "unit": UNIT, "steps": 1,
+                              "speedup_of_tiled": value / ws / plain_value}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -324,6 +347,7 @@ def main():
     ap.add_argument("--path", default="tiled", choices=["tiled", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--size", type=int, default=4096,
                     help="image side (4096 is the benchmark; smaller sides are for profiler captures)")
     ap.add_argument("--T", type=float, default=None,

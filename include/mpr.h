@@ -136,7 +136,8 @@ mpr_status mpr_get_image_info(const mpr_ctx* ctx, double* e_s, int64_t* n_sp, in
 
 /* Specific energy matching (Sec. 2.3, Alg. 2 step 3): for every image finds
  * T with e(T, L_T) = e_s, where e(T, L_T) = <H>/N_GP of an unconditional
- * simulation on an L_T x L_T lattice.  Newton iterations on the device use
+ * simulation on an L_T x L_T lattice started cold (every angle pi; Sec. 2.5
+ * names this start among those tested).  Newton iterations on the device use
  * the fluctuation relation d<e>/dT = N_GP Var(e) / T^2, safeguarded by a
  * bracket; every iteration re-equilibrates the lattices (warm start) and
  * averages n_meas sweeps over all chains.  The result becomes the context's

@@ -316,11 +316,13 @@ double oracle_adapt_a(double a, long n_acc, long n_gap, long i, double A_targ, d
 /* --------------------------------------------------- Sec. 2.3 SEM */
 
 /* Equilibrium specific energy e(T, L) of Eq. ene by unconditional simulation
- * (empty sample set) of K chains on an L x L lattice: hot start, n_eq sweeps
- * with the a-adaptation of Alg. 2, then n_meas sweeps with a frozen; the
- * specific energy H/N_GP of every measurement sweep of every chain is
- * averaged.  The variance of those values is returned in *var (nullable).
- * Chain k uses image tag img | 1 << 30 and chain index k. */
+ * (empty sample set) of K chains on an L x L lattice: cold start (every angle
+ * pi, the "ferromagnetic" start of Sec. 2.5, which reaches the low-temperature
+ * equilibrium far sooner than a random start), n_eq sweeps with the
+ * a-adaptation of Alg. 2, then n_meas sweeps with a frozen; the specific energy
+ * H/N_GP of every measurement sweep of every chain is averaged.  The variance
+ * of those values is returned in *var (nullable).  Chain k uses image tag
+ * img | 1 << 30 and chain index k. */
 double oracle_e_of_T(int L, int K, int n_eq, int n_meas, double q, double J, double T,
                      double A_targ, double k_a, uint64_t seed, uint32_t img, double* var)
 {
@@ -333,7 +335,7 @@ double oracle_e_of_T(int L, int K, int n_eq, int n_meas, double q, double J, dou
     long cnt = 0;
     uint32_t tag = img | (1u << 30);
     for (int k = 0; k < K; ++k) {
-        oracle_hot_start(L, L, gap, phi, seed, tag, (uint32_t)k);
+        for (long i = 0; i < n; ++i) phi[i] = OR_PI;
         double a = 1.0;
         for (int s = 0; s < n_eq; ++s) {
             long acc = oracle_sweep(L, L, phi, gap, q, J, T, a, seed, tag, (uint32_t)k,

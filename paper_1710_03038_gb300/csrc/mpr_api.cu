@@ -295,11 +295,11 @@ __global__ void sample_energy_kernel(const ImgDev* img, const float* samp, doubl
     }
 }
 
-// Hot start of the tiled state: slot -> 2 pi u with the site's first uniform
-// at sweep 0xFFFFFFFF; padding slots hold 0.
+// Start of the tiled state: hot (slot -> 2 pi u with the site's first uniform
+// at sweep 0xFFFFFFFF) or cold (every gap angle pi); padding slots hold 0.
 __global__ void hot_start_tiled_kernel(const ImgDev* img, const uint32_t* slot_pos, float* state,
                                        long long slots_img, int img_i, int n_chains, uint2 key,
-                                       uint32_t img_tag) {
+                                       uint32_t img_tag, int cold) {
     const ImgDev& I = img[img_i];
     const long long total = slots_img * n_chains;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -309,11 +309,15 @@ __global__ void hot_start_tiled_kernel(const ImgDev* img, const uint32_t* slot_p
         const uint32_t p = slot_pos[I.slot_off + k];
         float v = 0.0f;
         if (p != 0xFFFFFFFFu) {
-            const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
-            uint32_t wu, wr;
-            site_uniform_words(X, Y, (X + Y) & 1, 0xFFFFFFFFu, (uint32_t)chain,
-                               (uint32_t)img_i | img_tag, key, wu, wr);
-            v = kTwoPi * u24(wu);
+            if (cold) {
+                v = kPi;
+            } else {
+                const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
+                uint32_t wu, wr;
+                site_uniform_words(X, Y, (X + Y) & 1, 0xFFFFFFFFu, (uint32_t)chain,
+                                   (uint32_t)img_i | img_tag, key, wu, wr);
+                v = kTwoPi * u24(wu);
+            }
         }
         state[I.state_off + (long long)chain * I.stride + k] = v;
     }
@@ -826,8 +830,10 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
     const uint2 key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
     for (int i = 0; i < n_img; ++i) {
         if (tiled) {
+            // the temperature lattices start cold (see mpr_estimate_T), images hot
             hot_start_tiled_kernel<<<grid_for(c->slots[i] * n_chains), 256, 0, s>>>(
-                c->d_img, c->d_slot_pos, c->d_state, c->slots[i], i, n_chains, key, c->img_tag);
+                c->d_img, c->d_slot_pos, c->d_state, c->slots[i], i, n_chains, key, c->img_tag,
+                unconditional ? 1 : 0);
         } else {
             init_plain_kernel<<<grid_for((long long)Lx[i] * Ly[i] * n_chains), 256, 0, s>>>(
                 c->d_img, c->d_samp, c->d_state, i, n_chains, key, c->img_tag);

@@ -151,3 +151,47 @@ def test_fullsize_lognormal4096_32_chains():
 
 def test_fullsize_gamma8192_block_gap():
     _run("gamma8192")
+
+
+def test_autograd_on_512_crop_of_the_4096_field():
+    """Energy autograd on a 512^2 crop of the 4096^2 lognormal field (32 realisations):
+    torque and dH/dJ against central differences (h = 1e-3, FP64) and the oracle's gradient."""
+    w = synthetic.workload("lognormal4096")
+    z = torch.from_numpy(w.z[0]).cuda()
+    g = torch.from_numpy(w.gap[0]).cuda()
+    ctx = mpr.Context([z], [g], chains=32, params=mpr.Params(seed=SEED))
+    ctx.set_T([3e-3])
+    ctx.sweep(5, "equil")
+    crop = ctx.get_state()[0][:4, 1000:1512, 2000:2512].contiguous()  # 4 realisations
+    phi = crop.clone().requires_grad_(True)
+    J = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    H = mpr.MPREnergy.apply(phi, J)
+    wts = torch.tensor([1.0, -0.5, 0.25, 2.0], dtype=torch.float64, device="cuda")
+    (H * wts).sum().backward()
+    rng = np.random.default_rng(11)
+    for k in range(4):
+        p64 = crop[k].double().cpu().numpy()
+        assert abs(H[k].item() - oracle.energy(p64)) < 1e-6 * abs(H[k].item())
+        gk = phi.grad[k].cpu().numpy()
+        assert np.max(np.abs(gk - wts[k].item() * oracle.torque(p64))) < 2e-5
+        for _ in range(6):
+            y, x = int(rng.integers(0, 512)), int(rng.integers(0, 512))
+            e_p = p64.copy(); e_p[y, x] += 1e-3
+            e_m = p64.copy(); e_m[y, x] -= 1e-3
+            fd = (oracle.energy(e_p) - oracle.energy(e_m)) / 2e-3 * wts[k].item()
+            assert abs(gk[y, x] - fd) < 1e-5
+    dJ = sum(wts[k].item() * oracle.energy(crop[k].double().cpu().numpy()) for k in range(4))
+    assert abs(J.grad.item() - dJ) < 1e-6 * abs(dJ)
+
+
+def test_newton_T_matches_oracle_bisection_on_4096_field():
+    """SEM on the 4096^2 field's e_s: GPU Newton steps vs the oracle's bisection within 1%."""
+    w = synthetic.workload("lognormal4096")
+    z = torch.from_numpy(w.z[0]).cuda()
+    g = torch.from_numpy(w.gap[0]).cuda()
+    topts = mpr.TOpts(L=64, chains=8, n_equil=60, n_meas=120, iters=6)
+    ctx = mpr.Context([z], [g], chains=2, params=mpr.Params(seed=SEED), topts=topts)
+    T_gpu = ctx.estimate_T()[0]
+    e_s = ctx.image_info()["e_s"][0]
+    T_or = oracle.estimate_T(e_s, L=64, K=4, n_eq=150, n_meas=150, seed=SEED, rel_tol=2e-3)
+    assert abs(T_gpu - T_or) < 0.01 * T_or, (T_gpu, T_or)
