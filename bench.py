@@ -169,9 +169,12 @@ def run_gpu(args):
     g_d = torch.from_numpy(g_h).to(dev)
     z_pin = torch.from_numpy(z_h).pin_memory()
     g_pin = torch.from_numpy(g_h).pin_memory()
-    params = mpr.Params(seed=12345 + rank, path=args.path)
+    params = mpr.Params(seed=12345 + rank, path=args.path, use_graphs=not args.no_graphs)
     topts = mpr.TOpts()
-    stream = torch.cuda.current_stream(dev)
+    # a stream of our own: runs of sweeps are captured into CUDA graphs and replayed
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(stream)
 
     sweep_events = []
 
@@ -348,6 +351,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-graphs", action="store_true", help="launch sweeps without CUDA graphs")
     ap.add_argument("--size", type=int, default=4096,
                     help="image side (4096 is the benchmark; smaller sides are for profiler captures)")
     ap.add_argument("--T", type=float, default=None,

@@ -56,6 +56,10 @@ typedef enum {
     MPR_PATH_PLAIN = 1   /* dense per-chain planes, one thread per site, two passes  */
 } mpr_path;
 
+/* Pair interaction: the MPR bond -J cos(q dphi) (Eq. Hamiltonian_mod) or the
+ * GMRF bond J (dphi^2 / (2 pi^2) - 1) of Sec. 4.3. */
+typedef enum { MPR_MODEL_MPR = 0, MPR_MODEL_GMRF = 1 } mpr_model;
+
 /* Sweep phases of Alg. 2: equilibration (step 4, a adapted) and sampling
  * (step 5, a frozen, realisations accumulated). */
 typedef enum { MPR_EQUIL = 0, MPR_MEASURE = 1 } mpr_phase;
@@ -77,6 +81,12 @@ typedef struct {
     int tile_x, tile_y;      /* tiled path tile shape; 0 = autotuned                          */
     int chain_group;         /* tiled path: chains per thread block, even or >= n_chains;
                                 0 = automatic                                                  */
+    int literal_or;          /* 1: over-relaxation as printed in Eq. over-relax (q = 1 field,
+                                always applied), for comparison; plain path only; 0           */
+    int use_graphs;          /* 1: runs of 4 or more sweeps on a non-default stream are captured
+                                once into a CUDA graph and replayed; 1                         */
+    int model;               /* mpr_model; MPR_MODEL_GMRF runs on the plain path (its
+                                over-relaxation reflects about the neighbour mean); MPR        */
 } mpr_params;
 
 /* Options of the specific-energy-matching temperature estimate (Sec. 2.3). */
@@ -129,6 +139,18 @@ mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly,
                          const float* z, const uint8_t* gap, mpr_mem where,
                          void* workspace, size_t ws_bytes, mpr_stream stream);
 
+/* Autotuner of the tiled path: times `sweeps` equilibration sweeps of the
+ * given batch (after one warm-up sweep, temperature from the harmonic guess
+ * 4 (e_s + J)) for each candidate tile shape (32x16, 16x16, 32x32) and chain
+ * group (automatic, 8, 2) that fits `workspace`, and writes the fastest into
+ * p->tile_x, tile_y, chain_group.  timings (nullable, host [9]) receives
+ * milliseconds per sweep, tile-major, -1 for skipped candidates.  The
+ * workspace is scratch here (size it with mpr_workspace_size for 16x16
+ * tiles, the largest layout).  Blocking; the batch itself is not changed. */
+mpr_status mpr_autotune(int n_img, const int* Lx, const int* Ly, int n_chains, mpr_params* p,
+                        const float* z, const uint8_t* gap, mpr_mem where, void* workspace,
+                        size_t ws_bytes, int sweeps, double* timings, mpr_stream stream);
+
 /* Host copy of what init computed per image: e_s (nan when N_SP = 0), N_SP,
  * P (gap count), z_min, z_max.  Any pointer may be NULL. */
 mpr_status mpr_get_image_info(const mpr_ctx* ctx, double* e_s, int64_t* n_sp, int64_t* n_gap,
@@ -145,6 +167,25 @@ mpr_status mpr_get_image_info(const mpr_ctx* ctx, double* e_s, int64_t* n_sp, in
  * Errors: NO_SAMPLE_PAIRS, T_OUT_OF_RANGE (e_s >= -4J/pi^2 or <= -J). */
 mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_out, mpr_stream stream);
 
+/* The equilibrium specific energy e(T, L) of Eq. ene as a table (Sec. 2.3:
+ * computed once, then inverted for every sample): one unconditional L x L
+ * lattice per temperature T[k] (host [n_T], positive), `chains` chains each,
+ * cold start, n_equil sweeps with the a-adaptation, then the mean (e_out,
+ * host [n_T]) and variance (var_out, nullable) of H/N_GP over n_meas sweeps
+ * and all chains.  The lattices live in a caller workspace of
+ * mpr_eT_table_workspace_size() bytes.  Blocking. */
+mpr_status mpr_eT_table_workspace_size(int L, int n_T, int chains, size_t* bytes);
+mpr_status mpr_eT_table(int L, int n_T, const double* T, int chains, int n_equil, int n_meas,
+                        const mpr_params* p, void* workspace, size_t ws_bytes, double* e_out,
+                        double* var_out, mpr_stream stream);
+
+/* T_hat = e^-1(e_s | L) from a table (T, e) increasing in both (host [n_T]):
+ * linear interpolation in (e, log T) at every image's e_s, which becomes the
+ * context's temperature (T_out host [n_img], nullable).  Errors:
+ * T_OUT_OF_RANGE when e_s lies outside the table, NO_SAMPLE_PAIRS. */
+mpr_status mpr_set_T_from_table(mpr_ctx* ctx, int n_T, const double* T, const double* e,
+                                double* T_out, mpr_stream stream);
+
 /* Sets / reads the reduced temperature of every image (host [n_img]). */
 mpr_status mpr_set_T(mpr_ctx* ctx, const double* T, mpr_stream stream);
 mpr_status mpr_get_T(mpr_ctx* ctx, double* T, mpr_stream stream);
@@ -159,6 +200,23 @@ mpr_status mpr_get_T(mpr_ctx* ctx, double* T, mpr_stream stream);
  * MPR_MEASURE keeps a and adds every sweep's angles to the realisation
  * accumulators (Alg. 2 step 5).  flags: MPR_RECORD_ENERGY.  Asynchronous. */
 mpr_status mpr_sweep(mpr_ctx* ctx, int n_sweeps, int phase, int flags, mpr_stream stream);
+
+/* Equilibration with the automatic stop of Alg. 2 step 4 (Sec. 2.4-2.5):
+ * equilibration sweeps i = 0, 1, ... with energies recorded; once i >= n_fit,
+ * every n_f sweeps (i mod n_f == 0) the slope of the least-squares line
+ * (a Savitzky-Golay fit of degree 1) through the last n_fit chain-averaged
+ * specific energies of each image is taken; the run stops after the first
+ * check at which no image has a negative slope, or after sweep i_max.
+ * Paper defaults n_f = 5, n_fit = 20.  Blocking (one 4-byte read per check).
+ * n_done (nullable) receives the number of sweeps run.  2 <= n_fit <= 512. */
+mpr_status mpr_equilibrate(mpr_ctx* ctx, int n_f, int n_fit, int i_max, int* n_done,
+                           mpr_stream stream);
+
+/* The chain-averaged specific energies recorded by the last mpr_equilibrate:
+ * out host [n_img * MPR_HISTORY], image-major, entry (i mod MPR_HISTORY) for
+ * sweep i.  Blocking. */
+#define MPR_HISTORY 512
+mpr_status mpr_get_energy_history(mpr_ctx* ctx, double* out, mpr_stream stream);
 
 /* Specific energy H/N_GP (Eq. ene, FP64) of every realisation in its current
  * state, e_out [n_img * n_chains] (image-major) on the host (blocking) or the

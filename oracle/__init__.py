@@ -71,6 +71,15 @@ def _load():
                                       C.POINTER(d)]),
             "oracle_simulate": (i, [i, i, dp, u8, d, d, d, d, d, i, i, i, i, i, u64, u32s,
                                     dp, dpn, dpn, dpn]),
+            "oracle_sg_slope": (d, [dp, i]),
+            "oracle_gmrf_energy": (d, [i, i, dp, d]),
+            "oracle_gmrf_sample_energy": (lng, [i, i, dp, u8, d, C.POINTER(d)]),
+            "oracle_gmrf_site_update": (d, [d, dp, i, d, d, d, u64, u32s, u32s, u32s, i, i, i,
+                                            C.POINTER(i), dpn]),
+            "oracle_gmrf_sweep": (lng, [i, i, dp, u8, d, d, d, u64, u32s, u32s, u32s, dpn]),
+            "oracle_gmrf_simulate": (i, [i, i, dp, u8, d, d, d, d, i, i, i, u64, u32s, dp,
+                                         C.POINTER(d)]),
+            "oracle_equilibrate": (i, [i, i, dp, u8, d, d, d, d, d, i, i, i, i, u64, u32s, dp, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -269,3 +278,60 @@ def fill(z, gap, *, R, n_equil, n_meas, seed, img=0, T=None, sem=None, q=0.5, J=
     z_hat = np.where(np.asarray(gap) != 0, unmap(sim["phi_mean"], zmin, zmax),
                      np.asarray(z, dtype=np.float64))
     return dict(z_hat=z_hat, T=T, e_s=e_s, zmin=zmin, zmax=zmax)
+
+
+def sg_slope(y):
+    """Least-squares slope of a series against its index (degree-1 Savitzky-Golay)."""
+    y = _f64(y)
+    return _load().oracle_sg_slope(y, y.size)
+
+
+def equilibrate(phi_s, gap, *, T, R, seed, img=0, n_f=5, n_fit=20, i_max=500, q=0.5, J=1.0,
+                A_targ=0.3, k_a=3.0):
+    """Alg. 2 step 4 with the slope stop for R chains -> (sweeps run, chain-mean energies, states)."""
+    p = _f64(phi_s)
+    g = _u8(gap)
+    Ly, Lx = p.shape
+    out = np.zeros((R, Ly, Lx))
+    em = np.zeros(i_max + 1)
+    n = _load().oracle_equilibrate(Lx, Ly, p, g, q, J, T, A_targ, k_a, R, n_f, n_fit, i_max,
+                                   seed, img, out, em)
+    return int(n), em[:n], out
+
+
+# ------------------------------------------------------------ GMRF (Sec. 4.3)
+
+def gmrf_energy(phi, J=1.0):
+    """H = J sum_<ij> (dphi^2 / (2 pi^2) - 1) of the GMRF pair interaction."""
+    p = _f64(phi)
+    Ly, Lx = p.shape
+    return _load().oracle_gmrf_energy(Lx, Ly, p, J)
+
+
+def gmrf_sample_energy(phi, gap, J=1.0):
+    p = _f64(phi)
+    Ly, Lx = p.shape
+    e = C.c_double(np.nan)
+    n = _load().oracle_gmrf_sample_energy(Lx, Ly, p, _u8(gap), J, C.byref(e))
+    return e.value, int(n)
+
+
+def gmrf_sweep(phi, gap, *, T, a, seed, img=0, chain=0, sweep_index=0, J=1.0, diagnostics=False):
+    p = _f64(phi).copy()
+    Ly, Lx = p.shape
+    d = np.full((Ly, Lx, len(DIAG_FIELDS)), np.nan) if diagnostics else None
+    n = _load().oracle_gmrf_sweep(Lx, Ly, p, _u8(gap), J, T, a, seed, img, chain, sweep_index,
+                                  _ptr(d))
+    if diagnostics:
+        return p, int(n), {k: d[..., j] for j, k in enumerate(DIAG_FIELDS)}
+    return p, int(n)
+
+
+def gmrf_simulate(phi_s, gap, *, T, R, n_equil, n_meas, seed, img=0, J=1.0, A_targ=0.3, k_a=3.0):
+    p = _f64(phi_s)
+    Ly, Lx = p.shape
+    mean = np.zeros_like(p)
+    em = C.c_double()
+    _load().oracle_gmrf_simulate(Lx, Ly, p, _u8(gap), J, T, A_targ, k_a, R, n_equil, n_meas, seed,
+                                 img, mean, C.byref(em))
+    return dict(phi_mean=mean, e_mean=em.value)

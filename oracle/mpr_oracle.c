@@ -423,3 +423,189 @@ int oracle_simulate(int Lx, int Ly, const double* phi_s, const uint8_t* gap,
     free(acc);
     return 0;
 }
+
+/* Least-squares slope of y[0..n-1] against 0..n-1 (a Savitzky-Golay fit of
+ * degree 1, the reading taken for the unspecified degree of Sec. 2.4). */
+double oracle_sg_slope(const double* y, int n)
+{
+    double xm = 0.5 * (n - 1), ym = 0.0, sxy = 0.0, sxx = 0.0;
+    for (int k = 0; k < n; ++k) ym += y[k];
+    ym /= n;
+    for (int k = 0; k < n; ++k) { sxy += (k - xm) * (y[k] - ym); sxx += (k - xm) * (k - xm); }
+    return sxy / sxx;
+}
+
+/* Alg. 2 step 4 for R chains stepped together from their hot starts: sweep
+ * i, a-adaptation, chain-mean specific energy e(i+1); once i >= n_fit and
+ * i mod n_f == 0 the slope k of the last n_fit energies is taken and the
+ * loop ends when k >= 0, or after sweep i_max.  phi_out [R][N] receives the
+ * states, e_mean [i_max + 1] the chain-mean energies; returns sweeps run. */
+int oracle_equilibrate(int Lx, int Ly, const double* phi_s, const uint8_t* gap, double q,
+                       double J, double T, double A_targ, double k_a, int R, int n_f, int n_fit,
+                       int i_max, uint64_t seed, uint32_t img, double* phi_out, double* e_mean)
+{
+    long n = (long)Lx * Ly;
+    long P = 0;
+    for (long i = 0; i < n; ++i) P += gap[i] != 0;
+    double nb = (double)oracle_n_bonds(Lx, Ly);
+    double* a = (double*)malloc(sizeof(double) * R);
+    for (int c = 0; c < R; ++c) {
+        memcpy(phi_out + (long)c * n, phi_s, sizeof(double) * n);
+        oracle_hot_start(Lx, Ly, gap, phi_out + (long)c * n, seed, img, (uint32_t)c);
+        a[c] = 1.0;
+    }
+    int done = 0;
+    for (int i = 0; i <= i_max; ++i) {
+        double es = 0.0;
+        for (int c = 0; c < R; ++c) {
+            double* p = phi_out + (long)c * n;
+            long na = oracle_sweep(Lx, Ly, p, gap, q, J, T, a[c], seed, img, (uint32_t)c,
+                                   (uint32_t)i, 0, NULL);
+            a[c] = oracle_adapt_a(a[c], na, P, i, A_targ, k_a);
+            es += oracle_energy(Lx, Ly, p, q, J) / nb;
+        }
+        e_mean[i] = es / R;
+        done = i + 1;
+        if (i >= n_fit && i % n_f == 0 && oracle_sg_slope(e_mean + i + 1 - n_fit, n_fit) >= 0.0)
+            break;
+    }
+    free(a);
+    return done;
+}
+
+/* ------------------------------------------------ Sec. 4.3 GMRF variant */
+/* Pair interaction H_ij = -Dphi^2 / (2 pi^2) + 1 and H = -J sum H_ij, i.e.
+ * every bond costs J (Dphi^2 / (2 pi^2) - 1).  The site energy is quadratic
+ * in phi with its minimum at the mean m of the existing neighbours, so the
+ * over-relaxation reflects about m: phi' = 2 m - phi, kept when it stays in
+ * [0, 2 pi) (the reading taken; the paper does not spell the GMRF update
+ * out).  Everything else (checkerboard, proposal, acceptance, a schedule,
+ * random stream) is shared with the MPR sweep. */
+
+static double gmrf_bond(double d) { return d * d / (2.0 * OR_PI * OR_PI) - 1.0; }
+
+static double gmrf_site_energy(double v, const double* nbr, int n, double J)
+{
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += gmrf_bond(v - nbr[j]);
+    return J * s;
+}
+
+double oracle_gmrf_energy(int Lx, int Ly, const double* phi, double J)
+{
+    double sum = 0.0;
+    for (int y = 0; y < Ly; ++y)
+        for (int x = 0; x < Lx; ++x) {
+            long i = (long)y * Lx + x;
+            if (x + 1 < Lx) sum += gmrf_bond(phi[i] - phi[i + 1]);
+            if (y + 1 < Ly) sum += gmrf_bond(phi[i] - phi[i + Lx]);
+        }
+    return J * sum;
+}
+
+long oracle_gmrf_sample_energy(int Lx, int Ly, const double* phi, const uint8_t* gap, double J,
+                               double* e_s)
+{
+    double sum = 0.0;
+    long nsp = 0;
+    for (int y = 0; y < Ly; ++y)
+        for (int x = 0; x < Lx; ++x) {
+            long i = (long)y * Lx + x;
+            if (gap[i]) continue;
+            if (x + 1 < Lx && !gap[i + 1]) { sum += gmrf_bond(phi[i] - phi[i + 1]); ++nsp; }
+            if (y + 1 < Ly && !gap[i + Lx]) { sum += gmrf_bond(phi[i] - phi[i + Lx]); ++nsp; }
+        }
+    if (nsp > 0) *e_s = J * sum / (double)nsp;
+    return nsp;
+}
+
+double oracle_gmrf_site_update(double phi, const double* nbr, int n, double J, double T, double a,
+                               uint64_t seed, uint32_t img, uint32_t chain, uint32_t sweep, int x,
+                               int y, int colour, int* acc, double* d)
+{
+    double m = 0.0;
+    for (int j = 0; j < n; ++j) m += nbr[j];
+    m /= n;
+    double t = 2.0 * m - phi;
+    double p1 = (t >= 0.0 && t < OR_TWO_PI) ? t : phi;
+    double u, r;
+    site_uniforms(seed, img, chain, sweep, x, y, colour, &u, &r);
+    double raw = p1 + (OR_TWO_PI / a) * (u - 0.5);
+    double p2 = mod_two_pi(raw);
+    double dH = gmrf_site_energy(p2, nbr, n, J) - gmrf_site_energy(p1, nbr, n, J);
+    double ap = dH <= 0.0 ? 1.0 : exp(-dH / T);
+    int ok = r < ap;
+    if (d) {
+        double w0 = fabs(raw), w1 = fabs(raw - OR_TWO_PI);
+        double e0 = fabs(t), e1 = fabs(t - OR_TWO_PI);
+        double sens = 0.0;
+        for (int j = 0; j < n; ++j) sens += fabs(p2 - nbr[j]) + fabs(p1 - nbr[j]);
+        d[D_RMAP] = r - ap;
+        d[D_AP] = ap;
+        d[D_DHT] = dH / T;
+        d[D_ORSLACK] = e0 < e1 ? e0 : e1;
+        d[D_WRAPSLACK] = w0 < w1 ? w0 : w1;
+        d[D_FIELD] = (double)n;
+        d[D_SENS] = J * sens / (OR_PI * OR_PI * T);
+        d[D_ACC] = ok;
+    }
+    *acc = ok;
+    return ok ? p2 : p1;
+}
+
+long oracle_gmrf_sweep(int Lx, int Ly, double* phi, const uint8_t* gap, double J, double T,
+                       double a, uint64_t seed, uint32_t img, uint32_t chain, uint32_t sweep,
+                       double* diag)
+{
+    long n_acc = 0;
+    double nbr[4];
+    long nb[4];
+    for (int colour = 0; colour < 2; ++colour)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) {
+                if (((x + y) & 1) != colour) continue;
+                long i = (long)y * Lx + x;
+                if (!gap[i]) continue;
+                int n = neighbours(Lx, Ly, x, y, nb);
+                for (int j = 0; j < n; ++j) nbr[j] = phi[nb[j]];
+                int acc;
+                phi[i] = oracle_gmrf_site_update(phi[i], nbr, n, J, T, a, seed, img, chain, sweep,
+                                                 x, y, colour, &acc,
+                                                 diag ? diag + (long)D_N * i : NULL);
+                n_acc += acc;
+            }
+    return n_acc;
+}
+
+/* Conditional simulation of one image with the GMRF energy, like oracle_simulate. */
+int oracle_gmrf_simulate(int Lx, int Ly, const double* phi_s, const uint8_t* gap, double J,
+                         double T, double A_targ, double k_a, int R, int n_equil, int n_meas,
+                         uint64_t seed, uint32_t img, double* phi_mean, double* e_mean)
+{
+    long n = (long)Lx * Ly;
+    long P = 0;
+    for (long i = 0; i < n; ++i) P += gap[i] != 0;
+    double nb = (double)oracle_n_bonds(Lx, Ly);
+    double* phi = (double*)malloc(sizeof(double) * n);
+    double* acc = (double*)calloc((size_t)n, sizeof(double));
+    double esum = 0.0;
+    for (int c = 0; c < R; ++c) {
+        memcpy(phi, phi_s, sizeof(double) * n);
+        oracle_hot_start(Lx, Ly, gap, phi, seed, img, (uint32_t)c);
+        double a = 1.0;
+        for (int s = 0; s < n_equil + n_meas; ++s) {
+            long na = oracle_gmrf_sweep(Lx, Ly, phi, gap, J, T, a, seed, img, (uint32_t)c,
+                                        (uint32_t)s, NULL);
+            if (s < n_equil) a = oracle_adapt_a(a, na, P, s, A_targ, k_a);
+            else {
+                for (long i = 0; i < n; ++i) acc[i] += phi[i];
+                esum += oracle_gmrf_energy(Lx, Ly, phi, J) / nb;
+            }
+        }
+    }
+    for (long i = 0; i < n; ++i) phi_mean[i] = gap[i] ? acc[i] / ((double)R * n_meas) : phi_s[i];
+    if (e_mean) *e_mean = esum / ((double)R * n_meas);
+    free(phi);
+    free(acc);
+    return 0;
+}

@@ -41,6 +41,9 @@ class Params:
     path: str = "tiled"          # "tiled" (batched) or "plain"
     tile: tuple = (0, 0)         # (tile_x, tile_y); (0, 0) = automatic
     chain_group: int = 0         # chains per thread block; 0 = automatic
+    literal_or: bool = False     # printed q = 1 over-relaxation (plain path, comparison only)
+    use_graphs: bool = True      # replay captured CUDA graphs of sweep runs (non-default streams)
+    model: str = "mpr"           # "mpr" or "gmrf" (Sec. 4.3 pair interaction, plain path)
 
     def c(self) -> MprParams:
         p = MprParams()
@@ -51,6 +54,9 @@ class Params:
         p.path = {"tiled": _lib.MPR_PATH_TILED, "plain": _lib.MPR_PATH_PLAIN}[self.path]
         p.tile_x, p.tile_y = int(self.tile[0]), int(self.tile[1])
         p.chain_group = int(self.chain_group)
+        p.literal_or = int(bool(self.literal_or))
+        p.use_graphs = int(bool(self.use_graphs))
+        p.model = {"mpr": _lib.MPR_MODEL_MPR, "gmrf": _lib.MPR_MODEL_GMRF}[self.model]
         return p
 
 
@@ -187,6 +193,15 @@ class Context:
     def estimate_T_async(self, stream=None):
         call("mpr_estimate_T", self._ctx, None, _stream_ptr(stream))
 
+    def set_T_from_table(self, T_grid, e_grid, stream=None) -> np.ndarray:
+        """T_hat = e^-1(e_s) from an e(T) table (see eT_table); returns T per image."""
+        n = len(T_grid)
+        Tg = (C.c_double * n)(*[float(v) for v in T_grid])
+        eg = (C.c_double * n)(*[float(v) for v in e_grid])
+        out = (C.c_double * self.n_img)()
+        call("mpr_set_T_from_table", self._ctx, n, Tg, eg, out, _stream_ptr(stream))
+        return np.array(out[:])
+
     def set_T(self, T, stream=None):
         T = np.broadcast_to(np.asarray(T, dtype=np.float64), (self.n_img,))
         call("mpr_set_T", self._ctx, (C.c_double * self.n_img)(*T), _stream_ptr(stream))
@@ -201,6 +216,20 @@ class Context:
         ph = {"equil": _lib.MPR_EQUIL, "measure": _lib.MPR_MEASURE}[phase]
         call("mpr_sweep", self._ctx, int(n), ph, _lib.MPR_RECORD_ENERGY if record_energy else 0,
              _stream_ptr(stream))
+
+    def equilibrate(self, n_f: int = 5, n_fit: int = 20, i_max: int = 500, stream=None) -> int:
+        """Equilibrate until the degree-1 Savitzky-Golay slope of every image's
+        chain-mean energy is no longer negative (Alg. 2 step 4); returns sweeps run."""
+        n = C.c_int()
+        call("mpr_equilibrate", self._ctx, int(n_f), int(n_fit), int(i_max), C.byref(n),
+             _stream_ptr(stream))
+        return n.value
+
+    def energy_history(self, stream=None) -> np.ndarray:
+        """[n_img, 512] ring of chain-mean energies of the last equilibrate() (entry i % 512)."""
+        out = (C.c_double * (self.n_img * 512))()
+        call("mpr_get_energy_history", self._ctx, out, _stream_ptr(stream))
+        return np.array(out[:]).reshape(self.n_img, 512)
 
     def energy(self, stream=None) -> np.ndarray:
         out = (C.c_double * (self.n_img * self.chains))()
@@ -274,6 +303,47 @@ class Context:
     def set_sweep_index(self, sweep: int, equil_index: int, stream=None):
         call("mpr_set_sweep_index", self._ctx, C.c_uint32(sweep), C.c_uint32(equil_index),
              _stream_ptr(stream))
+
+
+def autotune(z, gap, chains: int, params: Params = None, sweeps: int = 3, device=None, stream=None):
+    """Time the tiled path's tile shapes and chain groups on this batch; returns
+    (tuned Params, {(tile, chain_group): ms per sweep})."""
+    import dataclasses
+    params = params or Params()
+    zs, gs = _as_list(z), _as_list(gap)
+    shapes = [tuple(int(v) for v in g.shape) for g in gs]
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    zf = torch.cat([torch.as_tensor(t, device=dev).reshape(-1).to(torch.float32) for t in zs]).contiguous()
+    gf = torch.cat([(torch.as_tensor(t, device=dev).reshape(-1) != 0).to(torch.uint8) for t in gs]).contiguous()
+    probe = dataclasses.replace(params, tile=(16, 16))
+    nbytes = workspace_size(shapes, None, chains, probe)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    p = params.c()
+    t = (C.c_double * 9)()
+    call("mpr_autotune", len(shapes), int_array([s[1] for s in shapes]),
+         int_array([s[0] for s in shapes]), int(chains), C.byref(p), _ptr(zf), _ptr(gf),
+         _lib.MPR_DEVICE, _ptr(ws), C.c_size_t(ws.numel()), int(sweeps), t, _stream_ptr(stream))
+    tiles = [(32, 16), (16, 16), (32, 32)]
+    groups = [0, 8, 2]
+    times = {(tiles[i // 3], groups[i % 3]): t[i] for i in range(9) if t[i] >= 0}
+    return dataclasses.replace(params, tile=(p.tile_x, p.tile_y), chain_group=p.chain_group), times
+
+
+def eT_table(T_grid, L: int = 256, chains: int = 16, n_equil: int = 60, n_meas: int = 60,
+             params: Params = None, device=None, stream=None):
+    """e(T, L) on unconditional L x L lattices at every T of T_grid -> (e, Var(e)) arrays."""
+    params = params or Params()
+    n = len(T_grid)
+    nbytes = C.c_size_t()
+    call("mpr_eT_table_workspace_size", int(L), n, int(chains), C.byref(nbytes))
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+    Tg = (C.c_double * n)(*[float(v) for v in T_grid])
+    e = (C.c_double * n)()
+    v = (C.c_double * n)()
+    call("mpr_eT_table", int(L), n, Tg, int(chains), int(n_equil), int(n_meas),
+         C.byref(params.c()), _ptr(ws), C.c_size_t(ws.numel()), e, v, _stream_ptr(stream))
+    return np.array(e[:]), np.array(v[:])
 
 
 def fill(z, gap, chains: int, n_equil: int, n_meas: int, params: Params = None,

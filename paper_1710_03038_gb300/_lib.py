@@ -21,6 +21,7 @@ STATUS = {
 MPR_DEVICE, MPR_HOST = 0, 1
 MPR_PATH_TILED, MPR_PATH_PLAIN = 0, 1
 MPR_EQUIL, MPR_MEASURE = 0, 1
+MPR_MODEL_MPR, MPR_MODEL_GMRF = 0, 1
 MPR_RECORD_ENERGY = 1
 
 # every symbol include/mpr.h declares
@@ -31,14 +32,16 @@ EXPORTS = (
     "mpr_reset_accumulators", "mpr_get_state", "mpr_set_state", "mpr_get_chain_info",
     "mpr_set_chain_a", "mpr_get_sweep_index", "mpr_set_sweep_index", "mpr_destroy",
     "mpr_lattice_energy", "mpr_lattice_torque", "mpr_philox", "mpr_math_probe",
-    "mpr_sample_energy_noalloc",
+    "mpr_sample_energy_noalloc", "mpr_equilibrate", "mpr_get_energy_history",
+    "mpr_eT_table_workspace_size", "mpr_eT_table", "mpr_set_T_from_table", "mpr_autotune",
 )
 
 
 class MprParams(C.Structure):
     _fields_ = [("q", C.c_double), ("J", C.c_double), ("A_targ", C.c_double), ("k_a", C.c_double),
                 ("seed", C.c_uint64), ("freeze_a_in_measure", C.c_int), ("path", C.c_int),
-                ("tile_x", C.c_int), ("tile_y", C.c_int), ("chain_group", C.c_int)]
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("chain_group", C.c_int),
+                ("literal_or", C.c_int), ("use_graphs", C.c_int), ("model", C.c_int)]
 
 
 class MprTOpts(C.Structure):
@@ -102,6 +105,12 @@ def load(path: str = LIB_PATH):
             "mpr_lattice_torque": (i, [i, ip, ip, vp, d, d, vp, vp, vp]),
             "mpr_philox": (i, [i, vp, u32p, vp, i, vp]),
             "mpr_math_probe": (i, [i, i, vp, vp, vp, vp]),
+            "mpr_equilibrate": (i, [vp, i, i, i, ip, vp]),
+            "mpr_get_energy_history": (i, [vp, dp, vp]),
+            "mpr_eT_table_workspace_size": (i, [i, i, i, C.POINTER(sz)]),
+            "mpr_eT_table": (i, [i, i, dp, i, i, i, pp, vp, sz, dp, dp, vp]),
+            "mpr_set_T_from_table": (i, [vp, i, dp, dp, dp, vp]),
+            "mpr_autotune": (i, [i, ip, ip, i, pp, vp, vp, i, vp, sz, i, dp, vp]),
             "mpr_sample_energy_noalloc": (i, [i, ip, ip, vp, vp, d, d, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():

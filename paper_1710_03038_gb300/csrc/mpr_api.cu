@@ -38,6 +38,7 @@ mpr_status fail(mpr_status s, const std::string& msg) {
     } while (0)
 
 constexpr size_t kAlign = 256;
+constexpr int kHist = 512;  // chain-mean energies kept per image for the equilibration test
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr double kPiD = 3.14159265358979323846;
 
@@ -47,7 +48,7 @@ constexpr double kPiD = 3.14159265358979323846;
 struct Layout {
     size_t img, ctl, ch_a, ch_cnt, ch_last, ch_ecur, ch_elast, ch_esum, ch_esum2;
     size_t zst, gst, outst, eout, samp, slot_map, tiles, counts, halo, scratch;
-    size_t slot_pos, acc1, acc2, state, newton, sub;
+    size_t slot_pos, acc1, acc2, state, newton, hist, sub;
     size_t total;
     long long n_slots;   // slot space over all images
     long long n_state;   // floats of the state buffer
@@ -130,6 +131,7 @@ Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_im
     L.acc2 = take(sizeof(double) * L.n_slots);
     L.state = take(sizeof(float) * L.n_state);
     L.newton = take(sizeof(double) * 4 * g.n_img);
+    L.hist = take(sizeof(double) * kHist * g.n_img + sizeof(int) * (g.n_img + 1));
     L.sub = take(sub_bytes);
     L.total = o;
     return L;
@@ -176,6 +178,8 @@ struct mpr_ctx {
     float* d_out = nullptr;
     double* d_eout = nullptr;
     double* d_newton = nullptr;
+    double* d_hist = nullptr;     // [n_img][kHist] chain-mean specific energy per sweep (ring)
+    int* d_sg = nullptr;          // [n_img] image settled, [n_img] = images still settling
     // host mirrors
     std::vector<ImgDev> h_img;
     std::vector<long long> slots;
@@ -185,7 +189,12 @@ struct mpr_ctx {
     long long n_meas_done = 0;
     bool T_set = false;
     mpr_ctx* sub = nullptr;   // unconditional lattices of the temperature estimate
-    ~mpr_ctx() { delete sub; }
+    // instantiated CUDA graphs of sweep sequences, keyed by (n, phase, flags, stats, accumulate)
+    std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
+    ~mpr_ctx() {
+        for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+        delete sub;
+    }
 };
 
 namespace {
@@ -218,6 +227,8 @@ void bind_views(mpr_ctx* c) {
     c->d_acc2 = at<double>(w, L.acc2);
     c->d_state = at<float>(w, L.state);
     c->d_newton = at<double>(w, L.newton);
+    c->d_hist = at<double>(w, L.hist);
+    c->d_sg = reinterpret_cast<int*>(c->d_hist + (size_t)kHist * c->g.n_img);
 }
 
 // ======================================================= init kernels
@@ -267,8 +278,12 @@ __global__ void map_kernel(const ImgDev* img, const float* z, const uint8_t* gap
 
 // Sample specific energy (Eq. mpr-sse) sums: -J sum cos(q dphi) over sample
 // pairs (right and down bonds), FP64.
+__device__ __forceinline__ double bond_energy(double d, double q, double J, int gmrf) {
+    return gmrf ? J * (d * d / (2.0 * kPiD * kPiD) - 1.0) : -J * cos(q * d);
+}
+
 __global__ void sample_energy_kernel(const ImgDev* img, const float* samp, double q, double J,
-                                     double* sums, unsigned long long* npairs) {
+                                     int gmrf, double* sums, unsigned long long* npairs) {
     const ImgDev& I = img[blockIdx.y];
     const long long n = (long long)I.Lx * I.Ly;
     double s = 0.0;
@@ -280,11 +295,11 @@ __global__ void sample_energy_kernel(const ImgDev* img, const float* samp, doubl
         const int x = (int)(i % I.Lx), y = (int)(i / I.Lx);
         if (x + 1 < I.Lx) {
             const float w = samp[I.site_off + i + 1];
-            if (w >= 0.0f) { s -= J * cos(q * ((double)v - (double)w)); ++cnt; }
+            if (w >= 0.0f) { s += bond_energy((double)v - (double)w, q, J, gmrf); ++cnt; }
         }
         if (y + 1 < I.Ly) {
             const float w = samp[I.site_off + i + I.Lx];
-            if (w >= 0.0f) { s -= J * cos(q * ((double)v - (double)w)); ++cnt; }
+            if (w >= 0.0f) { s += bond_energy((double)v - (double)w, q, J, gmrf); ++cnt; }
         }
     }
     s = warp_sum(s);
@@ -473,7 +488,7 @@ __device__ __forceinline__ float site_value(const ImgDev& I, const float* state,
 // H of every (image, chain) (blockIdx.y), FP64 sums of FP32 bond terms.
 __global__ void energy_kernel(const ImgDev* img, const float* state, const float* samp,
                               const int* slot_map, int tiled, int n_chains, float q, float J,
-                              double* out) {
+                              int gmrf, double* out) {
     const int ic = blockIdx.y;
     const int im = ic / n_chains, chain = ic - im * n_chains;
     const ImgDev& I = img[im];
@@ -484,10 +499,14 @@ __global__ void energy_kernel(const ImgDev* img, const float* state, const float
         const int x = (int)(i % I.Lx), y = (int)(i / I.Lx);
         const float v = site_value(I, state, samp, slot_map, tiled, chain, i);
         float e = 0.0f;
-        if (x + 1 < I.Lx)
-            e -= J * cosf(q * (v - site_value(I, state, samp, slot_map, tiled, chain, i + 1)));
-        if (y + 1 < I.Ly)
-            e -= J * cosf(q * (v - site_value(I, state, samp, slot_map, tiled, chain, i + I.Lx)));
+        if (x + 1 < I.Lx) {
+            const float d = v - site_value(I, state, samp, slot_map, tiled, chain, i + 1);
+            e += gmrf ? J * gmrf_bond(d) : -J * cosf(q * d);
+        }
+        if (y + 1 < I.Ly) {
+            const float d = v - site_value(I, state, samp, slot_map, tiled, chain, i + I.Lx);
+            e += gmrf ? J * gmrf_bond(d) : -J * cosf(q * d);
+        }
         s += (double)e;
     }
     s = warp_sum(s);
@@ -550,6 +569,43 @@ __global__ void predict_kernel(const ImgDev* img, const double* acc1, const doub
     }
 }
 
+// Chain-mean specific energy of every image after sweep i, into its ring.
+__global__ void sg_record_kernel(const ChainDev ch, double* hist, int n_img, int n_chains,
+                                 uint32_t i) {
+    const int im = blockIdx.x * blockDim.x + threadIdx.x;
+    if (im >= n_img) return;
+    double s = 0.0;
+    for (int k = 0; k < n_chains; ++k) s += ch.e_last[im * n_chains + k];
+    hist[(size_t)im * kHist + (i % kHist)] = s / n_chains;
+}
+
+// Savitzky-Golay slope of degree 1 (the least-squares line) through the last
+// n_fit chain-mean energies of every image, ending at sweep i; an image whose
+// slope is no longer negative has settled (Alg. 2 step 4.4).  sg[n_img]
+// receives how many images are still settling.
+__global__ void sg_check_kernel(const double* hist, int* sg, int n_img, int n_fit, uint32_t i) {
+    __shared__ int unsettled;
+    if (threadIdx.x == 0) unsettled = 0;
+    __syncthreads();
+    for (int im = threadIdx.x; im < n_img; im += blockDim.x) {
+        if (sg[im]) continue;
+        const double xm = 0.5 * (n_fit - 1);
+        double ym = 0.0;
+        for (int k = 0; k < n_fit; ++k) ym += hist[(size_t)im * kHist + ((i + 1 + k - n_fit) % kHist)];
+        ym /= n_fit;
+        double sxy = 0.0, sxx = 0.0;
+        for (int k = 0; k < n_fit; ++k) {
+            const double y = hist[(size_t)im * kHist + ((i + 1 + k - n_fit) % kHist)];
+            sxy += (k - xm) * (y - ym);
+            sxx += (k - xm) * (k - xm);
+        }
+        if (sxy / sxx >= 0.0) sg[im] = 1;
+        else atomicAdd(&unsettled, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sg[n_img] = unsettled;
+}
+
 __global__ void set_T_kernel(ImgDev* img, const double* T, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) { img[i].T = T[i]; img[i].invT = (float)(1.0 / T[i]); }
@@ -572,6 +628,12 @@ mpr_status check_params(const mpr_params* p) {
     if (p->path != MPR_PATH_TILED && p->path != MPR_PATH_PLAIN)
         return fail(MPR_ERR_INVALID_ARG, "unknown path");
     if (p->chain_group < 0) return fail(MPR_ERR_INVALID_ARG, "chain_group < 0");
+    if (p->model != MPR_MODEL_MPR && p->model != MPR_MODEL_GMRF)
+        return fail(MPR_ERR_INVALID_ARG, "unknown model");
+    if (p->model == MPR_MODEL_GMRF && p->path != MPR_PATH_PLAIN)
+        return fail(MPR_ERR_INVALID_ARG, "the GMRF variant runs on the plain path");
+    if (p->literal_or && p->path != MPR_PATH_PLAIN)
+        return fail(MPR_ERR_INVALID_ARG, "the printed (q = 1) over-relaxation runs on the plain path");
     return MPR_OK;
 }
 
@@ -626,7 +688,8 @@ mpr_status sub_workspace_size(const mpr_params& p, const mpr_T_opts& o, int n_im
     std::vector<int> L(n_img);
     for (int i = 0; i < n_img; ++i) L[i] = default_T_side(Lx[i], Ly[i], o);
     mpr_params sp = p;
-    sp.path = MPR_PATH_TILED;
+    sp.literal_or = 0;
+    sp.path = p.model == MPR_MODEL_GMRF ? MPR_PATH_PLAIN : MPR_PATH_TILED;
     sp.tile_x = sp.tile_y = 0;
     sp.chain_group = 0;
     return workspace_size_impl(n_img, L.data(), L.data(), nullptr, o.chains, sp, o, false, false,
@@ -853,7 +916,7 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
         unsigned long long* npairs = reinterpret_cast<unsigned long long*>(scratch + 3 * n_img);
         MPR_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 2 * n_img, s));
         sample_energy_kernel<<<dim3(grid_for(maxn, 256, 1024), n_img), 256, 0, s>>>(
-            c->d_img, c->d_samp, c->p.q, c->p.J, sums, npairs);
+            c->d_img, c->d_samp, c->p.q, c->p.J, c->p.model == MPR_MODEL_GMRF ? 1 : 0, sums, npairs);
         MPR_CUDA(cudaGetLastError());
         std::vector<double> h_sums(n_img);
         std::vector<unsigned long long> h_np(n_img);
@@ -876,8 +939,8 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
     return MPR_OK;
 }
 
-mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool accumulate,
-                      cudaStream_t s) {
+mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool accumulate,
+                         cudaStream_t s) {
     const bool equil = phase == MPR_EQUIL;
     const bool record = (flags & MPR_RECORD_ENERGY) != 0;
     SweepArgs a{};
@@ -908,6 +971,8 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
     int base = 0;
     if (!equil && accumulate) base |= kAccumulate | kAccumulate2;
     if (!equil && !c->p.freeze_a_in_measure) base |= kAlphaOne;
+    if (c->p.literal_or) base |= kLiteralOR;
+    if (c->p.model == MPR_MODEL_GMRF) base |= kGMRF;
     const bool tiled = c->g.path == MPR_PATH_TILED;
     for (int k = 0; k < n; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
@@ -924,9 +989,55 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
                                            tiled ? 1 : 0, c->p.A_targ, c->p.k_a);
         MPR_CUDA(cudaGetLastError());
     }
+    return MPR_OK;
+}
+
+// n sweeps: launched directly, or (sequences of at least 4 sweeps on a stream
+// that may be captured) through a CUDA graph captured once per context and
+// replayed.  Every argument of the launches is fixed for the context's life
+// (temperatures, a, the sweep counter live in device memory), so a graph
+// stays valid.
+mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool accumulate,
+                      cudaStream_t s) {
+    bool graph = c->p.use_graphs && n >= 4 && s != nullptr && s != cudaStreamLegacy;
+    if (graph) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            graph = false;  // the caller is capturing: launch into the caller's capture
+    }
+    if (!graph) {
+        MPR_TRY(launch_sweeps(c, n, phase, flags, stats, accumulate, s));
+    } else {
+        const long long key = ((long long)n << 8) | (phase << 4) | ((flags & 1) << 3) |
+                              ((stats ? 1 : 0) << 2) | ((accumulate ? 1 : 0) << 1);
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : c->graphs)
+            if (g.first == key) exec = g.second;
+        if (!exec) {
+            if (c->g.path == MPR_PATH_TILED) {
+                SweepArgs a{};
+                for (int col = 0; col < 2; ++col)
+                    MPR_CUDA(launch_tiled_pass(a, 0, c->g.tx, c->g.ty, c->kload[col], s, true));
+            }
+            MPR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const mpr_status st = launch_sweeps(c, n, phase, flags, stats, accumulate, s);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st != MPR_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+            const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ei));
+            c->graphs.emplace_back(key, exec);
+        }
+        MPR_CUDA(cudaGraphLaunch(exec, s));
+    }
     c->sweep += (uint32_t)n;
-    if (equil) c->equil_index += (uint32_t)n;
-    if (!equil && accumulate) c->n_meas_done += n;
+    if (phase == MPR_EQUIL) c->equil_index += (uint32_t)n;
+    if (phase != MPR_EQUIL && accumulate) c->n_meas_done += n;
     return MPR_OK;
 }
 
@@ -977,6 +1088,8 @@ mpr_status mpr_default_params(mpr_params* p) {
     p->seed = 0x2545F4914F6CDD1DULL;
     p->freeze_a_in_measure = 1;
     p->path = MPR_PATH_TILED;
+    p->use_graphs = 1;
+    p->model = MPR_MODEL_MPR;
     return MPR_OK;
 }
 
@@ -1037,7 +1150,8 @@ mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly,
     c->sub = new (std::nothrow) mpr_ctx();
     if (!c->sub) { delete c; return fail(MPR_ERR_INVALID_ARG, "out of host memory"); }
     c->sub->p = c->p;
-    c->sub->p.path = MPR_PATH_TILED;
+    c->sub->p.literal_or = 0;
+    c->sub->p.path = c->p.model == MPR_MODEL_GMRF ? MPR_PATH_PLAIN : MPR_PATH_TILED;
     c->sub->p.tile_x = c->sub->p.tile_y = 0;
     c->sub->p.chain_group = 0;
     c->sub->topt = c->topt;
@@ -1102,9 +1216,12 @@ mpr_status mpr_estimate_T(mpr_ctx* c, double* T_out, mpr_stream stream) {
     for (int i = 0; i < c->g.n_img; ++i) {
         const ImgDev& I = c->h_img[i];
         if (I.n_sp == 0) return fail(MPR_ERR_NO_SAMPLE_PAIRS, "image " + std::to_string(i) + " has no sample pairs");
-        if (!(I.e_s > -J && I.e_s < -4.0 * J / (kPiD * kPiD)))
+        // e(T) runs from -J (T = 0) to the independent-angle value: -4J/pi^2 for
+        // the MPR bond, J (1/3 - 1) for the GMRF bond
+        const double e_inf = c->p.model == MPR_MODEL_GMRF ? -2.0 * J / 3.0 : -4.0 * J / (kPiD * kPiD);
+        if (!(I.e_s > -J && I.e_s < e_inf))
             return fail(MPR_ERR_T_OUT_OF_RANGE, "image " + std::to_string(i) +
-                                                    ": e_s outside (-J, -4J/pi^2)");
+                                                    ": e_s outside the range of e(T)");
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     mpr_ctx* u = c->sub;
@@ -1134,6 +1251,185 @@ mpr_status mpr_sweep(mpr_ctx* c, int n_sweeps, int phase, int flags, mpr_stream 
     return run_sweeps(c, n_sweeps, phase, flags, false, true, reinterpret_cast<cudaStream_t>(stream));
 }
 
+mpr_status mpr_autotune(int n_img, const int* Lx, const int* Ly, int n_chains, mpr_params* p,
+                        const float* z, const uint8_t* gap, mpr_mem where, void* workspace,
+                        size_t ws_bytes, int sweeps, double* timings, mpr_stream stream) {
+    MPR_TRY(validate_shapes(n_img, Lx, Ly, n_chains));
+    MPR_TRY(check_params(p));
+    if (p->path != MPR_PATH_TILED) return fail(MPR_ERR_INVALID_ARG, "the autotuner serves the tiled path");
+    if (!z || !gap || sweeps < 1) return fail(MPR_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    static const int tiles[3][2] = {{32, 16}, {16, 16}, {32, 32}};
+    const int groups[3] = {0, 8, 2};
+    double best = 1e300;
+    int bt = -1, bg = 0;
+    for (int ti = 0; ti < 3; ++ti) {
+        for (int gi = 0; gi < 3; ++gi) {
+            double* slot = timings ? timings + ti * 3 + gi : nullptr;
+            if (slot) *slot = -1.0;
+            int cg = groups[gi];
+            if (cg > 0 && cg >= n_chains) continue;  // same as covering every chain
+            mpr_ctx c;
+            c.p = *p;
+            c.p.tile_x = tiles[ti][0];
+            c.p.tile_y = tiles[ti][1];
+            c.p.chain_group = cg;
+            c.p.use_graphs = 0;
+            mpr_default_T_opts(&c.topt);
+            // the candidate must fit the workspace and the tile's per-lane limit
+            if (init_impl(&c, n_img, Lx, Ly, n_chains, z, gap, where, workspace, ws_bytes, false,
+                          s) != MPR_OK)
+                continue;
+            std::vector<double> T(n_img);
+            for (int i = 0; i < n_img; ++i) {
+                const double e_s = std::isfinite(c.h_img[i].e_s) ? c.h_img[i].e_s : -0.9;
+                T[i] = std::min(10.0, std::max(1e-4, 4.0 * (e_s + p->J)));
+            }
+            MPR_TRY(mpr_set_T(&c, T.data(), stream));
+            MPR_TRY(run_sweeps(&c, 1, MPR_EQUIL, 0, false, false, s));
+            cudaEvent_t e0, e1;
+            MPR_CUDA(cudaEventCreate(&e0));
+            MPR_CUDA(cudaEventCreate(&e1));
+            MPR_CUDA(cudaEventRecord(e0, s));
+            const mpr_status st = run_sweeps(&c, sweeps, MPR_EQUIL, 0, false, false, s);
+            MPR_CUDA(cudaEventRecord(e1, s));
+            MPR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st != MPR_OK) return st;
+            MPR_TRY(check_device_status(&c, s));
+            const double per = ms / sweeps;
+            if (slot) *slot = per;
+            if (per < best) { best = per; bt = ti; bg = cg; }
+        }
+    }
+    if (bt < 0) return fail(MPR_ERR_WORKSPACE, "no tile shape fits the workspace");
+    p->tile_x = tiles[bt][0];
+    p->tile_y = tiles[bt][1];
+    p->chain_group = bg;
+    return MPR_OK;
+}
+
+mpr_status mpr_eT_table_workspace_size(int L, int n_T, int chains, size_t* bytes) {
+    if (!bytes || L < 2 || L > 65535 || n_T < 1 || chains < 1 || (long long)n_T * chains > 65535)
+        return fail(MPR_ERR_INVALID_ARG, "need 2 <= L <= 65535, n_T >= 1, chains >= 1");
+    mpr_params p;
+    mpr_default_params(&p);
+    mpr_T_opts o;
+    mpr_default_T_opts(&o);
+    std::vector<int> Ls(n_T, L);
+    return workspace_size_impl(n_T, Ls.data(), Ls.data(), nullptr, chains, p, o, false, false, bytes);
+}
+
+mpr_status mpr_eT_table(int L, int n_T, const double* T, int chains, int n_equil, int n_meas,
+                        const mpr_params* p, void* workspace, size_t ws_bytes, double* e_out,
+                        double* var_out, mpr_stream stream) {
+    if (!T || !e_out || n_equil < 0 || n_meas < 1) return fail(MPR_ERR_INVALID_ARG, "bad arguments");
+    MPR_TRY(check_params(p));
+    size_t need = 0;
+    MPR_TRY(mpr_eT_table_workspace_size(L, n_T, chains, &need));
+    if (ws_bytes < need) return fail(MPR_ERR_WORKSPACE, "workspace too small for the e(T) table");
+    for (int k = 0; k < n_T; ++k)
+        if (!(T[k] > 0.0) || !std::isfinite(T[k])) return fail(MPR_ERR_INVALID_ARG, "T must be positive");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    mpr_ctx u;
+    u.p = *p;
+    u.p.path = MPR_PATH_TILED;
+    u.p.literal_or = 0;
+    u.p.tile_x = u.p.tile_y = 0;
+    u.p.chain_group = 0;
+    mpr_default_T_opts(&u.topt);
+    std::vector<int> Ls(n_T, L);
+    MPR_TRY(init_impl(&u, n_T, Ls.data(), Ls.data(), chains, nullptr, nullptr, MPR_DEVICE, workspace,
+                      ws_bytes, true, s));
+    u.img_tag = 1u << 29;  // a stream of its own
+    MPR_CUDA(cudaMemcpyAsync(u.d_newton, T, sizeof(double) * n_T, cudaMemcpyHostToDevice, s));
+    set_T_kernel<<<grid_for(n_T), 256, 0, s>>>(u.d_img, u.d_newton, n_T);
+    MPR_CUDA(cudaGetLastError());
+    MPR_TRY(run_sweeps(&u, n_equil, MPR_EQUIL, 0, false, false, s));
+    MPR_TRY(run_sweeps(&u, n_meas, MPR_MEASURE, MPR_RECORD_ENERGY, true, false, s));
+    const int nc = n_T * chains;
+    std::vector<double> s1(nc), s2(nc);
+    MPR_CUDA(cudaMemcpyAsync(s1.data(), u.ch.e_sum, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    MPR_CUDA(cudaMemcpyAsync(s2.data(), u.ch.e_sum2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    MPR_CUDA(cudaStreamSynchronize(s));
+    MPR_TRY(check_device_status(&u, s));
+    for (int k = 0; k < n_T; ++k) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < chains; ++j) { a += s1[k * chains + j]; b += s2[k * chains + j]; }
+        const double n = (double)chains * n_meas;
+        e_out[k] = a / n;
+        if (var_out) var_out[k] = std::max(b / n - (a / n) * (a / n), 0.0);
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_set_T_from_table(mpr_ctx* c, int n_T, const double* T, const double* e,
+                                double* T_out, mpr_stream stream) {
+    if (!c || !T || !e || n_T < 2) return fail(MPR_ERR_INVALID_ARG, "need a table of >= 2 points");
+    for (int k = 1; k < n_T; ++k)
+        if (!(T[k] > T[k - 1]) || !(e[k] > e[k - 1]))
+            return fail(MPR_ERR_INVALID_ARG, "the table must increase in T and in e");
+    std::vector<double> out(c->g.n_img);
+    for (int i = 0; i < c->g.n_img; ++i) {
+        const double es = c->h_img[i].e_s;
+        if (c->h_img[i].n_sp == 0) return fail(MPR_ERR_NO_SAMPLE_PAIRS, "image without sample pairs");
+        if (!(es >= e[0] && es <= e[n_T - 1]))
+            return fail(MPR_ERR_T_OUT_OF_RANGE, "e_s of image " + std::to_string(i) +
+                                                    " lies outside the table");
+        int k = 0;
+        while (k + 2 < n_T && e[k + 1] < es) ++k;
+        // linear in (e, log T) between the bracketing points
+        const double w = (es - e[k]) / (e[k + 1] - e[k]);
+        out[i] = std::exp(std::log(T[k]) + w * (std::log(T[k + 1]) - std::log(T[k])));
+    }
+    MPR_TRY(mpr_set_T(c, out.data(), stream));
+    if (T_out) std::copy(out.begin(), out.end(), T_out);
+    return MPR_OK;
+}
+
+mpr_status mpr_equilibrate(mpr_ctx* c, int n_f, int n_fit, int i_max, int* n_done,
+                           mpr_stream stream) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_f < 1 || n_fit < 2 || n_fit > kHist || i_max < 1)
+        return fail(MPR_ERR_INVALID_ARG, "need n_f >= 1, 2 <= n_fit <= 512, i_max >= 1");
+    if (!c->T_set) return fail(MPR_ERR_STATE, "temperature not set: call mpr_estimate_T or mpr_set_T");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int n_img = c->g.n_img;
+    MPR_CUDA(cudaMemsetAsync(c->d_sg, 0, sizeof(int) * (n_img + 1), s));
+    int done = 0;
+    for (int i = 0; i <= i_max; ++i) {
+        // sweep i of this equilibration (Alg. 2 step 4.1-4.3), energies recorded
+        MPR_TRY(run_sweeps(c, 1, MPR_EQUIL, MPR_RECORD_ENERGY, false, true, s));
+        sg_record_kernel<<<grid_for(n_img), 256, 0, s>>>(c->ch, c->d_hist, n_img, c->g.n_chains,
+                                                          (uint32_t)i);
+        MPR_CUDA(cudaGetLastError());
+        done = i + 1;
+        if (i >= n_fit && i % n_f == 0) {
+            sg_check_kernel<<<1, 256, 0, s>>>(c->d_hist, c->d_sg, n_img, n_fit, (uint32_t)i);
+            MPR_CUDA(cudaGetLastError());
+            int unsettled = 0;
+            MPR_CUDA(cudaMemcpyAsync(&unsettled, c->d_sg + n_img, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MPR_CUDA(cudaStreamSynchronize(s));
+            if (unsettled == 0) break;
+        }
+    }
+    if (n_done) *n_done = done;
+    return check_device_status(c, s);
+}
+
+mpr_status mpr_get_energy_history(mpr_ctx* c, double* out, mpr_stream stream) {
+    static_assert(kHist == MPR_HISTORY, "history length");
+    if (!c || !out) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MPR_CUDA(cudaMemcpyAsync(out, c->d_hist, sizeof(double) * kHist * c->g.n_img,
+                             cudaMemcpyDeviceToHost, s));
+    MPR_CUDA(cudaStreamSynchronize(s));
+    return MPR_OK;
+}
+
 mpr_status mpr_energy(mpr_ctx* c, double* e_out, mpr_mem where, mpr_stream stream) {
     if (!c || !e_out) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1144,7 +1440,7 @@ mpr_status mpr_energy(mpr_ctx* c, double* e_out, mpr_mem where, mpr_stream strea
     for (int i = 0; i < c->g.n_img; ++i) maxn = std::max(maxn, (long long)c->g.Lx[i] * c->g.Ly[i]);
     energy_kernel<<<dim3(grid_for(maxn, 256, 512), nc), 256, 0, s>>>(
         c->d_img, c->d_state, c->d_samp, c->d_slot_map, c->g.path == MPR_PATH_TILED ? 1 : 0,
-        c->g.n_chains, (float)c->p.q, (float)c->p.J, d_out);
+        c->g.n_chains, (float)c->p.q, (float)c->p.J, c->p.model == MPR_MODEL_GMRF ? 1 : 0, d_out);
     MPR_CUDA(cudaGetLastError());
     energy_finish_kernel<<<grid_for(nc), 256, 0, s>>>(c->d_img, d_out, c->g.n_chains, nc);
     MPR_CUDA(cudaGetLastError());

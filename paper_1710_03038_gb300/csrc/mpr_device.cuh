@@ -125,29 +125,16 @@ struct UpdateOut {
     bool accepted;
 };
 
-// One application of Alg. 1 to a gap site with angle phi whose neighbours
-// give the field (C, S) = sum_j (cos q phi_j, sin q phi_j).
-//  1. over-relaxation (Eq. over-relax, q-consistent): Psi = atan2(S, C),
-//     theta' = (2 Psi - q phi) mod 2 pi, phi' = theta'/q if theta' < 2 pi q;
-//  2-3. proposal phi'' = (phi' + alpha (u - 1/2)) mod 2 pi, alpha = 2 pi / a;
-//  4. dH = -J R [cos(q phi'' - Psi) - cos(q phi' - Psi)]
-//        = 2 J R sin(x + h) sin(h), x = q phi' - Psi, h = q (phi'' - phi') / 2
+// The restricted Metropolis half of Alg. 1 (steps 2-6) for a spin at phi1
+// (after over-relaxation) in the field of length R and angle Psi:
+//  2-3. proposal phi'' = (phi1 + alpha (u - 1/2)) mod 2 pi, alpha = 2 pi / a;
+//  4. dH = -J R [cos(q phi'' - Psi) - cos(q phi1 - Psi)]
+//        = 2 J R sin(x + h) sin(h), x = q phi1 - Psi, h = q (phi'' - phi1) / 2
 //     (product form: no cancellation for small steps);
 //  5-6. accept iff r < exp(-dH / T) (always when dH <= 0).
-__device__ __forceinline__ UpdateOut hybrid_update(float phi, float C, float S, uint32_t wu,
-                                                   uint32_t wr, const UpdateConst& k,
-                                                   float alpha, float invT) {
-    const float R2 = fmaf(C, C, S * S);
-    float Psi = 0.0f;
-    float phi1 = phi;
-    float R = 0.0f;
-    if (R2 > kFieldEps2) {
-        Psi = atan2_poly(S, C);
-        R = R2 * rsqrtf(R2);
-        float t = fmaf(2.0f, Psi, -k.q * phi);
-        t = fmaf(-kTwoPi, floorf(t * kInvTwoPi), t);
-        if (t >= 0.0f && t < k.two_pi_q) phi1 = t * k.inv_q;
-    }
+__device__ __forceinline__ UpdateOut metropolis_step(float phi1, float Psi, float R, uint32_t wu,
+                                                     uint32_t wr, const UpdateConst& k,
+                                                     float alpha, float invT) {
     const float u = u24(wu);
     const float r = u24(wr);
     float phi2 = fmaf(alpha, u - 0.5f, phi1);
@@ -165,6 +152,80 @@ __device__ __forceinline__ UpdateOut hybrid_update(float phi, float C, float S, 
     o.x_new = acc ? x + 2.0f * h : x;
     o.accepted = acc;
     return o;
+}
+
+// One application of Alg. 1 to a gap site with angle phi whose neighbours
+// give the field (C, S) = sum_j (cos q phi_j, sin q phi_j): over-relaxation
+// (Eq. over-relax, q-consistent): Psi = atan2(S, C), theta' = (2 Psi - q phi)
+// mod 2 pi, phi' = theta'/q if theta' < 2 pi q (else phi' = phi); then the
+// restricted Metropolis step.
+__device__ __forceinline__ UpdateOut hybrid_update(float phi, float C, float S, uint32_t wu,
+                                                   uint32_t wr, const UpdateConst& k,
+                                                   float alpha, float invT) {
+    const float R2 = fmaf(C, C, S * S);
+    float Psi = 0.0f;
+    float phi1 = phi;
+    float R = 0.0f;
+    if (R2 > kFieldEps2) {
+        Psi = atan2_poly(S, C);
+        R = R2 * rsqrtf(R2);
+        float t = fmaf(2.0f, Psi, -k.q * phi);
+        t = fmaf(-kTwoPi, floorf(t * kInvTwoPi), t);
+        if (t >= 0.0f && t < k.two_pi_q) phi1 = t * k.inv_q;
+    }
+    return metropolis_step(phi1, Psi, R, wu, wr, k, alpha, invT);
+}
+
+// Alg. 1 with the over-relaxation formula as printed (Eq. over-relax with the
+// q = 1 field (C1, S1) = sum_j (cos phi_j, sin phi_j)): phi' = (2 Phi - phi)
+// mod 2 pi, Phi = atan2(S1, C1), always applied; the Metropolis step still
+// uses the MPR energy through its field (C, S).
+__device__ __forceinline__ UpdateOut literal_update(float phi, float C, float S, float C1, float S1,
+                                                    uint32_t wu, uint32_t wr, const UpdateConst& k,
+                                                    float alpha, float invT) {
+    const float R2 = fmaf(C, C, S * S);
+    float Psi = 0.0f, R = 0.0f;
+    if (R2 > kFieldEps2) {
+        Psi = atan2_poly(S, C);
+        R = R2 * rsqrtf(R2);
+    }
+    float phi1 = phi;
+    if (fmaf(C1, C1, S1 * S1) > kFieldEps2) {
+        float t = fmaf(2.0f, atan2_poly(S1, C1), -phi);
+        phi1 = fmaf(-kTwoPi, floorf(t * kInvTwoPi), t);
+        if (phi1 >= kTwoPi || phi1 < 0.0f) phi1 = 0.0f;
+    }
+    return metropolis_step(phi1, Psi, R, wu, wr, k, alpha, invT);
+}
+
+// Alg. 1 with the GMRF pair interaction of Sec. 4.3 (every bond costs
+// J (dphi^2 / (2 pi^2) - 1)): the site energy is quadratic with its minimum at
+// the mean m of the n existing neighbours, so over-relaxation reflects about
+// it, phi' = 2m - phi, kept inside [0, 2 pi); the proposal and acceptance are
+// those of the MPR step, with
+// dH = J n (phi'' - phi')(phi'' + phi' - 2m) / (2 pi^2) (a product: no cancellation).
+__device__ __forceinline__ UpdateOut gmrf_update(float phi, float m, float n, uint32_t wu,
+                                                 uint32_t wr, float J, float alpha, float invT) {
+    const float t = fmaf(2.0f, m, -phi);
+    const float phi1 = (t >= 0.0f && t < kTwoPi) ? t : phi;
+    const float u = u24(wu);
+    const float r = u24(wr);
+    float phi2 = fmaf(alpha, u - 0.5f, phi1);
+    if (phi2 < 0.0f) phi2 += kTwoPi;
+    else if (phi2 >= kTwoPi) phi2 -= kTwoPi;
+    constexpr float kInvTwoPi2 = 0.050660591821168885f;  // 1 / (2 pi^2)
+    const float dH = J * n * kInvTwoPi2 * (phi2 - phi1) * ((phi2 + phi1) - 2.0f * m);
+    const bool acc = (dH <= 0.0f) || (r < __expf(-dH * invT));
+    UpdateOut o;
+    o.phi = acc ? phi2 : phi1;
+    o.R = 0.0f;
+    o.x_new = 0.0f;
+    o.accepted = acc;
+    return o;
+}
+
+__device__ __forceinline__ float gmrf_bond(float d) {
+    return fmaf(d * d, 0.050660591821168885f, -1.0f);
 }
 
 // Energy of a site after its update: -J R cos(x_new).

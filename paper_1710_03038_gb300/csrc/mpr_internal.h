@@ -66,6 +66,8 @@ enum SweepFlags : int {
     kAccumulate = 2,   // add the new angles to the realisation accumulators
     kAccumulate2 = 4,  // also squares
     kAlphaOne = 8,     // a = 1 (printed Alg. 2 step 5.2)
+    kLiteralOR = 16,   // printed q = 1 over-relaxation formula (plain path only)
+    kGMRF = 32,        // GMRF pair interaction of Sec. 4.3 (plain path only)
 };
 
 struct SweepArgs {
@@ -96,8 +98,9 @@ struct SweepArgs {
 mpr_status set_last_error(mpr_status s, const std::string& msg);
 
 // ---- launchers ------------------------------------------------------------
+// setup_only: set the kernel's attributes without launching (before a capture)
 cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tile_x, int tile_y,
-                              int kload, cudaStream_t s);
+                              int kload, cudaStream_t s, bool setup_only = false);
 cudaError_t launch_plain_pass(const SweepArgs& a, int max_Lx, int max_Ly, cudaStream_t s);
 bool tiled_config_supported(int tile_x, int tile_y);
 int tiled_max_kload(int tile_x, int tile_y);  // largest per-lane site count a tile shape serves

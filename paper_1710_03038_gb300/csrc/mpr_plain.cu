@@ -71,7 +71,28 @@ plain_pass_kernel(SweepArgs a) {
             site_uniform_words(x, y, colour, sweep, (uint32_t)chain, (uint32_t)img | a.img_tag,
                                a.key, wu, wr);
             UpdateConst k{a.q, a.inv_q, a.two_pi_q, a.J};
-            const UpdateOut o = hybrid_update(phi_now, C, S, wu, wr, k, alpha, I.invT);
+            UpdateOut o;
+            if (a.flags & kGMRF) {
+                float sum = 0.0f, cnt = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    sum += has[j] ? nb[j] : 0.0f;
+                    cnt += has[j] ? 1.0f : 0.0f;
+                }
+                o = gmrf_update(phi_now, sum / cnt, cnt, wu, wr, a.J, alpha, I.invT);
+            } else if (a.flags & kLiteralOR) {
+                float C1 = 0.0f, S1 = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float s1, c1;
+                    sincosf(nb[j], &s1, &c1);
+                    C1 += has[j] ? c1 : 0.0f;
+                    S1 += has[j] ? s1 : 0.0f;
+                }
+                o = literal_update(phi_now, C, S, C1, S1, wu, wr, k, alpha, I.invT);
+            } else {
+                o = hybrid_update(phi_now, C, S, wu, wr, k, alpha, I.invT);
+            }
             P[i] = o.phi;
             phi_now = o.phi;
             n_acc = o.accepted;
@@ -82,9 +103,15 @@ plain_pass_kernel(SweepArgs a) {
         }
         if (a.flags & kEnergy) {
             // every bond has exactly one end of the second colour
+            if (a.flags & kGMRF) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                e_site += has[j] ? -a.J * __cosf(a.q * (phi_now - nb[j])) : 0.0f;
+                for (int j = 0; j < 4; ++j)
+                    e_site += has[j] ? a.J * gmrf_bond(phi_now - nb[j]) : 0.0f;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    e_site += has[j] ? -a.J * __cosf(a.q * (phi_now - nb[j])) : 0.0f;
+            }
         }
     }
     const long long slot =

@@ -424,7 +424,7 @@ __global__ void tile_halo_kernel(const ImgDev* img, TileDesc* tiles, const int* 
 }
 
 template <int TX, int TY, int NW, int K>
-cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s) {
+cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
     using Cfg = TiledCfg<TX, TY, NW>;
     static_assert(Cfg::smem_max <= 227 * 1024, "shared memory");
     static bool attr_set = false;
@@ -435,6 +435,7 @@ cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    if (setup_only) return cudaSuccess;
     if (a.gt < 1 || a.gt > Cfg::GT) return cudaErrorInvalidValue;
     dim3 grid(n_tiles, (a.n_chains + a.chain_group - 1) / a.chain_group);
     tiled_pass_kernel<TX, TY, NW, K><<<grid, Cfg::NT, Cfg::smem_for(a.gt), s>>>(a);
@@ -453,22 +454,22 @@ int tiled_max_kload(int tx, int ty) {
 
 // kload = largest gap count of one colour over the pass's tiles, over 32, rounded up.
 cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, int kload,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool setup_only) {
     if (a.chain_group % 2 != 0 && a.chain_group < a.n_chains) return cudaErrorInvalidValue;
     if (tx == 32 && ty == 16) {
-        if (kload <= 3) return launch_cfg<32, 16, 8, 3>(a, n_tiles, s);
-        if (kload <= 4) return launch_cfg<32, 16, 8, 4>(a, n_tiles, s);
-        if (kload <= 5) return launch_cfg<32, 16, 8, 5>(a, n_tiles, s);
-        if (kload <= 6) return launch_cfg<32, 16, 8, 6>(a, n_tiles, s);
-        return launch_cfg<32, 16, 8, 8>(a, n_tiles, s);
+        if (kload <= 3) return launch_cfg<32, 16, 8, 3>(a, n_tiles, s, setup_only);
+        if (kload <= 4) return launch_cfg<32, 16, 8, 4>(a, n_tiles, s, setup_only);
+        if (kload <= 5) return launch_cfg<32, 16, 8, 5>(a, n_tiles, s, setup_only);
+        if (kload <= 6) return launch_cfg<32, 16, 8, 6>(a, n_tiles, s, setup_only);
+        return launch_cfg<32, 16, 8, 8>(a, n_tiles, s, setup_only);
     }
     if (tx == 16 && ty == 16) {
-        if (kload <= 2) return launch_cfg<16, 16, 4, 2>(a, n_tiles, s);
-        return launch_cfg<16, 16, 4, 4>(a, n_tiles, s);
+        if (kload <= 2) return launch_cfg<16, 16, 4, 2>(a, n_tiles, s, setup_only);
+        return launch_cfg<16, 16, 4, 4>(a, n_tiles, s, setup_only);
     }
     if (tx == 32 && ty == 32) {
-        if (kload <= 8) return launch_cfg<32, 32, 8, 8>(a, n_tiles, s);
-        return launch_cfg<32, 32, 8, 16>(a, n_tiles, s);
+        if (kload <= 8) return launch_cfg<32, 32, 8, 8>(a, n_tiles, s, setup_only);
+        return launch_cfg<32, 32, 8, 16>(a, n_tiles, s, setup_only);
     }
     return cudaErrorInvalidValue;
 }

@@ -1,0 +1,221 @@
+"""Rows after the hot path: automatic equilibration stop and the paper-literal switches."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1710_03038_gb300 as mpr  # noqa: E402
+
+SEED = 0xBEEF1234
+
+
+def _grf64():
+    w = synthetic.workload("grf64")
+    return w.z[0], w.gap[0]
+
+
+def test_equilibrate_applies_the_slope_rule_and_matches_the_oracle():
+    z, g = _grf64()
+    T, R = 0.13, 10
+    ctx = mpr.Context([z], [g], chains=R, params=mpr.Params(seed=SEED))
+    ctx.set_T([T])
+    n = ctx.equilibrate(n_f=5, n_fit=20, i_max=300)
+    hist = ctx.energy_history()[0][:n]
+    assert 21 <= n <= 301
+    checks = [i for i in range(n) if i >= 20 and i % 5 == 0]
+    for i in checks[:-1]:
+        assert oracle.sg_slope(hist[i + 1 - 20:i + 1]) < 0
+    if n <= 300:
+        assert oracle.sg_slope(hist[n - 20:n]) >= 0
+    # the recorded chain means are the chains' energies
+    e = ctx.energy()[0]
+    assert abs(hist[n - 1] - e.mean()) < 1e-6
+    phi, _, _ = oracle.map_to_angles(z.astype(np.float64), g)
+    n_o, em, _ = oracle.equilibrate(phi, g, T=T, R=R, seed=SEED, n_f=5, n_fit=20, i_max=300)
+    # different random trajectories after the first near-threshold decision:
+    # the stopping sweep and the energy reached agree statistically
+    assert abs(n - n_o) <= 60, (n, n_o)
+    assert abs(hist[n - 1] - em[n_o - 1]) < 4e-3, (hist[n - 1], em[n_o - 1])
+
+
+def test_literal_over_relaxation_sweep_parity():
+    z, g = _grf64()
+    ctx = mpr.Context([z], [g], chains=2, params=mpr.Params(seed=SEED, path="plain", literal_or=True))
+    ctx.set_T([0.13])
+    ctx.sweep(3, "equil")
+    before = ctx.get_state()[0].cpu().numpy()
+    a = ctx.chain_info()["a"][0]
+    s_idx, _ = ctx.sweep_index()
+    ctx.sweep(1, "equil")
+    after = ctx.get_state()[0].cpu().numpy()
+    for c in range(2):
+        ref, _, diag = oracle.sweep(before[c].astype(np.float64), g, T=0.13, a=float(a[c]),
+                                    seed=SEED, chain=c, sweep_index=s_idx, literal_or=True,
+                                    diagnostics=True)
+        d = np.abs(ref - after[c])[g == 1]
+        assert np.mean(d > 1e-5) < 0.01
+
+
+def test_literal_switches_bias_study():
+    """The printed over-relaxation (q = 1 field) and a = 1 while sampling, against the default.
+
+    The printed reflection does not conserve the q = 1/2 energy, so the chain
+    leaves the MPR Gibbs measure: its mean energy sits measurably away from the
+    default's.  Prints the deviations of <e> and MAE."""
+    z, g = _grf64()
+    T, R, ne, nm = 0.13, 10, 200, 100
+    m = g == 1
+    out = {}
+    for name, kw in (("default", dict(path="plain")),
+                     ("literal_or", dict(path="plain", literal_or=True)),
+                     ("a_one_in_measure", dict(path="plain", freeze_a_in_measure=False))):
+        ctx = mpr.Context([z], [g], chains=R, params=mpr.Params(seed=SEED, **kw))
+        ctx.set_T([T])
+        ctx.sweep(ne, "equil")
+        es = []
+        for _ in range(nm):
+            ctx.sweep(1, "measure", record_energy=True)
+            es.append(ctx.chain_info()["e_last"][0])
+        es = np.array(es)
+        zh = ctx.predict()[0].cpu().numpy()
+        mae = float(np.mean(np.abs(zh[m] - z[m])))
+        out[name] = (es.mean(), es.mean(0).std(ddof=1) / math.sqrt(R), mae)
+    print({k: tuple(round(float(x), 6) for x in v) for k, v in out.items()})
+    e0, s0, mae0 = out["default"]
+    e1, s1, mae1 = out["literal_or"]
+    assert abs(e1 - e0) > 5 * math.hypot(s0, s1)  # the printed reflection biases <e>
+    e2, s2, mae2 = out["a_one_in_measure"]
+    assert abs(e2 - e0) < 5 * math.hypot(s0, s2) + 1e-3  # a = 1 keeps the measure
+
+
+def test_eT_table_matches_oracle_and_inverts_to_the_bisection_T():
+    """e(T, L) table on unconditional lattices (Sec. 2.3) against the oracle's
+    e(T), and T_hat from the table against the oracle's bisection."""
+    L = 64
+    # ratio 1.12 between neighbours: linear interpolation in (e, log T) errs ~0.2%
+    T_grid = np.geomspace(2e-3, 2.0, 60)
+    e, var = mpr.eT_table(T_grid, L=L, chains=16, n_equil=80, n_meas=80,
+                          params=mpr.Params(seed=SEED))
+    assert np.all(np.diff(e) > 0)
+    for k in (8, 30, 52):
+        m_o, v_o = oracle.e_of_T(T_grid[k], L=L, K=4, n_eq=100, n_meas=200, seed=SEED)
+        # standard errors from the per-sweep variance (correlated sweeps: x4)
+        se = math.sqrt(var[k] / (16 * 80) * 4 + v_o / (4 * 200) * 4)
+        assert se > 0
+        assert abs(e[k] - m_o) < 4 * se + 1e-5, (T_grid[k], e[k], m_o, se)
+    z, g = _grf64()
+    ctx = mpr.Context([z], [g], chains=2, params=mpr.Params(seed=SEED))
+    T_tab = ctx.set_T_from_table(T_grid, e)[0]
+    e_s = ctx.image_info()["e_s"][0]
+    T_or = oracle.estimate_T(e_s, L=L, K=4, n_eq=100, n_meas=150, seed=SEED, rel_tol=2e-3)
+    assert abs(T_tab - T_or) < 0.01 * T_or, (T_tab, T_or)
+    # out of the table's range
+    with pytest.raises(mpr._lib.MprError) as err:
+        ctx.set_T_from_table(T_grid[:5], e[:5])
+    assert err.value.status == 5
+
+
+def _ragged():
+    shapes = [(130, 97), (64, 64), (45, 200)]
+    zs, gs = [], []
+    for k, (h, w) in enumerate(shapes):
+        z = synthetic.grf((h, w), nu=0.5, ell=8.0, mean=50, std=10, seed=500 + k)
+        g = synthetic.uniform_gaps((h, w), 0.35 + 0.1 * k, 600 + k)
+        zs.append(z.astype(np.float32))
+        gs.append(g.astype(np.uint8))
+    return zs, gs
+
+
+def test_graph_replay_equals_direct_launches():
+    """Sweep runs captured into CUDA graphs and replayed give the same bits."""
+    zs, gs = _ragged()
+    side = torch.cuda.Stream()
+    out = []
+    for use_graphs in (True, False):
+        with torch.cuda.stream(side):
+            ctx = mpr.Context(zs, gs, chains=6,
+                              params=mpr.Params(seed=SEED, use_graphs=use_graphs))
+            ctx.set_T([0.2, 0.15, 0.3])
+            ctx.sweep(6, "equil", record_energy=True)
+            ctx.sweep(5, "measure")
+            ctx.sweep(5, "measure")  # replays the cached graph
+            st = [s.clone() for s in ctx.get_state()]
+            zh = [p.clone() for p in ctx.predict()]
+            info = ctx.chain_info()
+        side.synchronize()
+        out.append((st, zh, info))
+    for a, b in zip(out[0][0], out[1][0]):
+        assert torch.equal(a, b)
+    for a, b in zip(out[0][1], out[1][1]):
+        assert torch.equal(a, b)
+    assert np.array_equal(out[0][2]["a"], out[1][2]["a"])
+
+
+def test_autotune_picks_a_valid_configuration():
+    zs, gs = _ragged()
+    tuned, times = mpr.autotune(zs, gs, chains=8, params=mpr.Params(seed=SEED), sweeps=2)
+    assert times and min(times.values()) > 0
+    key = (tuple(tuned.tile), tuned.chain_group)
+    assert key in times and times[key] == min(times.values())
+    ref = mpr.Context(zs, gs, chains=8, params=mpr.Params(seed=SEED))
+    got = mpr.Context(zs, gs, chains=8, params=tuned)
+    for c in (ref, got):
+        c.set_T([0.2, 0.15, 0.3])
+        c.sweep(3, "equil")
+    for a, b in zip(ref.get_state(), got.get_state()):
+        assert torch.equal(a, b)
+
+
+def test_gmrf_sweep_parity():
+    z, g = _grf64()
+    ctx = mpr.Context([z], [g], chains=2, params=mpr.Params(seed=SEED, path="plain", model="gmrf"))
+    ctx.set_T([0.1])
+    ctx.sweep(3, "equil")
+    before = ctx.get_state()[0].cpu().numpy()
+    a = ctx.chain_info()["a"][0]
+    s_idx, _ = ctx.sweep_index()
+    ctx.sweep(1, "equil", record_energy=True)
+    after = ctx.get_state()[0].cpu().numpy()
+    e_rec = ctx.chain_info()["e_last"][0]
+    e_now = ctx.energy()[0]
+    for c in range(2):
+        ref, _, diag = oracle.gmrf_sweep(before[c].astype(np.float64), g, T=0.1, a=float(a[c]),
+                                         seed=SEED, chain=c, sweep_index=s_idx, diagnostics=True)
+        d = np.abs(ref - after[c])[g == 1]
+        assert np.mean(d > 1e-5) < 0.01
+        e_ref = oracle.gmrf_energy(after[c].astype(np.float64)) / oracle.n_bonds(64, 64)
+        assert abs(e_rec[c] - e_ref) < 2e-6 and abs(e_now[c] - e_ref) < 2e-6
+    info = ctx.image_info()
+    phi, _, _ = oracle.map_to_angles(z.astype(np.float64), g)
+    assert abs(info["e_s"][0] - oracle.gmrf_sample_energy(phi, g)[0]) < 1e-6
+
+
+def test_mpr_beats_gmrf_on_lognormal_data():
+    """Sec. 4.3 (Table lognormal): on lognormal data the MPR prediction errors are
+    smaller than the GMRF's, each with its SEM temperature."""
+    maes = {"mpr": [], "gmrf": []}
+    for seed in (70, 71):
+        z = synthetic.lognormal_grf((64, 64), nu=0.5, ell=5.0, log_mean=5.0, log_std=1.0, seed=seed)
+        z = z.astype(np.float32)
+        g = synthetic.uniform_gaps((64, 64), 0.33, seed + 100).astype(np.uint8)
+        m = g == 1
+        for model in ("mpr", "gmrf"):
+            ctx = mpr.Context([z], [g], chains=10,
+                              params=mpr.Params(seed=SEED, path="plain", model=model),
+                              topts=mpr.TOpts(L=64, chains=8, n_equil=60, n_meas=60, iters=5))
+            ctx.estimate_T()
+            ctx.sweep(100, "equil")
+            ctx.sweep(100, "measure")
+            zh = ctx.predict()[0].cpu().numpy()
+            maes[model].append(float(np.mean(np.abs(zh[m] - z[m]))))
+    print(maes)
+    assert np.mean(maes["mpr"]) < np.mean(maes["gmrf"])

@@ -426,3 +426,78 @@ def test_estimate_T_inverts_e_of_T():
         oracle.estimate_T(-0.3, **kw)  # above the infinite-temperature energy
     with pytest.raises(ValueError):
         oracle.estimate_T(-1.01, **kw)  # below the ground state
+
+
+# ------------------------------------------- equilibration stop, Alg. 2 step 4
+
+def test_sg_slope_closed_forms():
+    """Degree-1 Savitzky-Golay slope: exact on lines, zero on symmetric series."""
+    x = np.arange(20, dtype=float)
+    assert oracle.sg_slope(3.0 - 0.25 * x) == pytest.approx(-0.25)
+    assert oracle.sg_slope((x - 9.5) ** 2) == pytest.approx(0.0, abs=1e-12)
+    assert oracle.sg_slope(np.cos(np.linspace(0, 2 * np.pi, 21))[:-1] * 0 + 7.0) == pytest.approx(0.0)
+
+
+def test_equilibrate_stops_at_the_first_non_negative_slope():
+    phi, gap = _gappy(24, 0.5, 30)
+    n, em, _ = oracle.equilibrate(phi, gap, T=0.2, R=3, seed=31, n_f=5, n_fit=20, i_max=300)
+    assert 21 <= n <= 301
+    checks = [i for i in range(n) if i >= 20 and i % 5 == 0]
+    for i in checks[:-1]:
+        assert oracle.sg_slope(em[i + 1 - 20:i + 1]) < 0
+    if n <= 300:
+        assert checks[-1] == n - 1 and oracle.sg_slope(em[n - 20:n]) >= 0
+    # the energy went down from the hot start
+    assert em[-1] < em[0]
+
+
+# ------------------------------------------------------ GMRF variant, Sec. 4.3
+
+def test_gmrf_energy_closed_forms():
+    """Every bond costs J (dphi^2/(2 pi^2) - 1): aligned -> -J per bond, contrast pi -> -J/2."""
+    assert oracle.gmrf_energy(np.full((4, 5), 1.3), J=2.0) == pytest.approx(-2.0 * oracle.n_bonds(5, 4))
+    assert oracle.gmrf_energy(np.array([[0.0, math.pi]])) == pytest.approx(-0.5)
+    assert oracle.gmrf_energy(np.array([[0.0, TWO_PI]])) == pytest.approx(1.0)
+    e, n = oracle.gmrf_sample_energy(np.array([[0.0, math.pi, 0.0]]), np.zeros((1, 3), np.uint8))
+    assert n == 2 and e == pytest.approx(-0.5)
+
+
+def test_gmrf_zero_temperature_never_raises_energy():
+    phi, gap = _gappy(16, 0.5, 40)
+    H = oracle.gmrf_energy(phi)
+    for s in range(30):
+        phi, _ = oracle.gmrf_sweep(phi, gap, T=1e-300, a=2.0, seed=41, sweep_index=s)
+        H1 = oracle.gmrf_energy(phi)
+        assert H1 <= H + 1e-11
+        H = H1
+
+
+def test_gmrf_three_site_marginal_by_quadrature():
+    """Middle spin between two samples: a Gaussian truncated to [0, 2 pi) by 1-D quadrature."""
+    T = 0.5
+    ea, eb = 1.0, 4.0
+    dens = lambda v: math.exp(-(((v - ea) ** 2 + (v - eb) ** 2) / (2 * math.pi ** 2) - 2) / T)
+    Z = integrate.quad(dens, 0, TWO_PI, limit=200)[0]
+    m1 = integrate.quad(lambda v: v * dens(v), 0, TWO_PI, limit=200)[0] / Z
+    gap = np.array([[0, 1, 0]], np.uint8)
+    phi = oracle.hot_start(np.array([[ea, 0.0, eb]]), gap, seed=42, img=0, chain=0)
+    xs = []
+    for s in range(40200):
+        phi, _ = oracle.gmrf_sweep(phi, gap, T=T, a=2.0, seed=43, sweep_index=s)
+        if s >= 200:
+            xs.append(phi[0, 1])
+    mean, err = _batch_mean_err(xs)
+    assert abs(mean - m1) < 4 * err + 1e-3, (mean, m1, err)
+
+
+def test_gmrf_high_temperature_limit():
+    """Independent uniform angles: E[dphi^2] = 2 (2 pi)^2 / 12, so e -> 1/3 - 1 = -2/3."""
+    L = 12
+    gap = np.ones((L, L), np.uint8)
+    phi = oracle.hot_start(np.zeros((L, L)), gap, seed=44, img=0, chain=0)
+    es = []
+    for s in range(600):
+        phi, _ = oracle.gmrf_sweep(phi, gap, T=1e8, a=1.0, seed=45, sweep_index=s)
+        es.append(oracle.gmrf_energy(phi) / oracle.n_bonds(L, L))
+    m, err = _batch_mean_err(es)
+    assert abs(m + 2.0 / 3.0) < 4 * err + 2e-3
