@@ -142,7 +142,8 @@ __device__ __forceinline__ UpdateOut metropolis_step(float phi1, float Psi, floa
     else if (phi2 >= kTwoPi) phi2 -= kTwoPi;
     const float x = fmaf(k.q, phi1, -Psi);
     const float h = 0.5f * k.q * (phi2 - phi1);
-    const float s1 = __sinf(wrap_pi(x + h));
+    // x + h lies in (-3 pi/2, 5 pi/2): the hardware sine reduces that range itself
+    const float s1 = __sinf(x + h);
     const float s2 = sin_taylor(h);
     const float dH = 2.0f * k.J * R * s1 * s2;
     const bool acc = (dH <= 0.0f) || (r < __expf(-dH * invT));

@@ -457,11 +457,11 @@ cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, i
                               cudaStream_t s, bool setup_only) {
     if (a.chain_group % 2 != 0 && a.chain_group < a.n_chains) return cudaErrorInvalidValue;
     if (tx == 32 && ty == 16) {
-        if (kload <= 3) return launch_cfg<32, 16, 8, 3>(a, n_tiles, s, setup_only);
-        if (kload <= 4) return launch_cfg<32, 16, 8, 4>(a, n_tiles, s, setup_only);
-        if (kload <= 5) return launch_cfg<32, 16, 8, 5>(a, n_tiles, s, setup_only);
-        if (kload <= 6) return launch_cfg<32, 16, 8, 6>(a, n_tiles, s, setup_only);
-        return launch_cfg<32, 16, 8, 8>(a, n_tiles, s, setup_only);
+        if (kload <= 3) return launch_cfg<32, 16, 4, 3>(a, n_tiles, s, setup_only);
+        if (kload <= 4) return launch_cfg<32, 16, 4, 4>(a, n_tiles, s, setup_only);
+        if (kload <= 5) return launch_cfg<32, 16, 4, 5>(a, n_tiles, s, setup_only);
+        if (kload <= 6) return launch_cfg<32, 16, 4, 6>(a, n_tiles, s, setup_only);
+        return launch_cfg<32, 16, 4, 8>(a, n_tiles, s, setup_only);
     }
     if (tx == 16 && ty == 16) {
         if (kload <= 2) return launch_cfg<16, 16, 4, 2>(a, n_tiles, s, setup_only);
