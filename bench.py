@@ -42,6 +42,22 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(units_per_rank_step, steps, world_size, ms_max):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank_step * steps * world_size / (ms_max / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -114,18 +130,25 @@ def _oracle_worker(args):
     return P * sweeps, time.perf_counter() - t0
 
 
-def cpu_baseline(workers=None, crop=2048, sweeps=1):
-    """The FP64 oracle on the host cores: one sweep of a crop of the input per worker process."""
-    import tempfile
+def _crop(crop):
     import numpy as np
     import oracle
     import synthetic
-    oracle.build()
-    workers = workers or min(os.cpu_count() or 1, 16)
     w = synthetic.workload("lognormal4096")
     z = w.z[0][:crop, :crop].astype(np.float64)
     g = w.gap[0][:crop, :crop]
     phi, _, _ = oracle.map_to_angles(z, g)
+    return phi, g, int(w.gap[0].sum())
+
+
+def cpu_baseline(workers=None, crop=2048, sweeps=1, data=None):
+    """The FP64 oracle on the host cores: one sweep of a crop of the input per worker process."""
+    import tempfile
+    import numpy as np
+    import oracle
+    oracle.build()
+    workers = workers or min(os.cpu_count() or 1, 16)
+    phi, g, _ = data if data is not None else _crop(crop)
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "crop.npz")
         np.savez(path, phi=phi, gap=g)
@@ -137,9 +160,9 @@ def cpu_baseline(workers=None, crop=2048, sweeps=1):
     units = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     return {"value": units / busy, "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": f"{sweeps} hybrid sweep(s) of a {crop}x{crop} crop of the 4096^2 input, "
-                      f"one realisation per worker, {workers} worker processes "
-                      f"({units} gap site-updates, {wall:.1f} s wall)"}
+            "sample": f"{sweeps} hybrid sweep(s) of a {phi.shape[0]}x{phi.shape[1]} crop of the "
+                      f"4096^2 input, one realisation per worker, {workers} worker processes "
+                      f"({units} gap site-updates, {wall:.1f} s wall)", "wall_s": wall}
 
 
 # ------------------------------------------------------------ GPU arm
@@ -241,15 +264,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1)
 
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
 
     units_step = (ne + nm) * P * R
-    value = units_step * args.steps * ws / (ms / 1e3)
-    e2e = units_step * args.steps * ws / (ms_e2e / 1e3)
+    value = job_throughput(units_step, args.steps, ws, ms)
+    e2e = job_throughput(units_step, args.steps, ws, ms_e2e)
     sweep_ms = [a.elapsed_time(b) for a, b in sweep_events]
     launch_ms = statistics.mean(sweep_ms) / 2.0  # two colour passes per sweep
     peak, peak_kind = _peaks()
@@ -307,6 +326,7 @@ def run_gpu(args):
                               "speedup_of_tiled": value / ws / plain_value}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"].pop("wall_s", None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -315,22 +335,24 @@ def run_gpu(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores (rank 0 only)."""
     ws, rank, _ = _dist()
     if rank != 0:
-        return
-    import synthetic
-    w = synthetic.workload("lognormal4096")
-    times, units = [], 0
+        return None
+    data = _crop(1024)
+    P = data[2]
+    vals, walls = [], []
     cb = None
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(crop=1024)
+        cb = cpu_baseline(crop=1024, data=data)
         if k >= args.warmup:
-            times.append(cb["value"])
-    value = statistics.mean(times)
-    P = int(w.gap[0].sum())
+            vals.append(cb["value"])
+            walls.append(cb["wall_s"])
+    value = statistics.mean(vals)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD, "sample": "oracle sweeps on crops of the input"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
@@ -339,6 +361,7 @@ def run_reference(args):
         "gap_sites": P,
     }
     print(json.dumps(line), flush=True)
+    return line
 
 
 def main():

@@ -359,3 +359,45 @@ def test_host_errors():
     assert e.value.status == 7  # T not set
     with pytest.raises(mpr._lib.MprError):
         ctx.predict()
+
+
+def _tiny_images():
+    """Degenerate shapes: 2x2 with one gap, single-row and single-column-pair
+    images, 3x3, and a nearly empty image (two samples left)."""
+    rng = np.random.default_rng(9)
+    out = []
+    for (h, w, frac) in ((2, 2, 0.25), (2, 9, 0.5), (9, 2, 0.5), (3, 3, 0.6), (7, 11, 0.95)):
+        z = rng.normal(50, 10, (h, w)).astype(np.float32)
+        g = synthetic.uniform_gaps((h, w), frac, int(rng.integers(1 << 30))).astype(np.uint8)
+        if (g == 0).sum() < 2:  # keep at least two samples
+            g.ravel()[:2] = 0
+        out.append((z, g))
+    return [o[0] for o in out], [o[1] for o in out]
+
+
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_degenerate_shapes_sweep_parity(path):
+    zs, gs = _tiny_images()
+    R = 3
+    ctx = make_ctx(zs, gs, R, path)
+    T = np.array([0.3, 0.2, 0.25, 0.15, 0.4])
+    ctx.set_T(T)
+    ctx.sweep(2, "equil")
+    for _ in range(3):
+        before = [s.cpu().numpy() for s in ctx.get_state()]
+        a = ctx.chain_info()["a"]
+        s_idx, _ = ctx.sweep_index()
+        ctx.sweep(1, "equil", record_energy=True)
+        after = [s.cpu().numpy() for s in ctx.get_state()]
+        info = ctx.chain_info()
+        for i, g in enumerate(gs):
+            for c in range(R):
+                compare_sweep(before[i][c], after[i][c], g, T=T[i], a=a[i, c], seed=SEED, img=i,
+                              chain=c, sweep_index=s_idx)
+                e_ref = oracle.specific_energy(after[i][c].astype(np.float64))
+                assert abs(info["e_last"][i, c] - e_ref) < 2e-6
+    ctx.sweep(4, "measure")
+    for z, g, p in zip(zs, gs, ctx.predict()):
+        p = p.cpu().numpy()
+        assert np.array_equal(p[g == 0], z[g == 0])
+        assert np.all(np.isfinite(p))
