@@ -60,7 +60,9 @@ struct TiledCfg {
 
 // K: gap sites per lane and realisation that one pass can meet (the largest
 // own or other-colour count of the pass's tiles, over 32, rounded up).
-template <int TX, int TY, int NW, int K>
+// ACC: sampling pass that adds every new angle (and its square) to the
+// realisation sums; equilibration passes are compiled without that code.
+template <int TX, int TY, int NW, int K, bool ACC>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))  // 64 registers: 32 warps per SM
 tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     using Cfg = TiledCfg<TX, TY, NW>;
@@ -98,8 +100,8 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const int ng = min(a.chain_group, a.n_chains - r0);
     const uint32_t* spos = a.slot_pos + I.slot_off;
     const float* samp = a.samp + I.site_off;
-    const bool accum = (a.flags & kAccumulate) != 0;
-    const bool accum2 = (a.flags & kAccumulate2) != 0;
+    constexpr bool accum = ACC;
+    const bool accum2 = ACC && (a.flags & kAccumulate2) != 0;
     const uint32_t sweep = a.ctl->sweep;
     const uint32_t c3 = (uint32_t)t_img | a.img_tag | ((uint32_t)c << 31);
     const UpdateConst uk{a.q, a.inv_q, a.two_pi_q, a.J};
@@ -109,7 +111,8 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
 
     // -- prologue ---------------------------------------------------------------
     for (int i = tid; i < EXT; i += NT) cellmap[i] = 0;
-    for (int i = tid; i < 2 * NMAX; i += NT) acc_s[i] = 0.0f;
+    if (accum)
+        for (int i = tid; i < 2 * NMAX; i += NT) acc_s[i] = 0.0f;
     for (int i = tid; i < 2 * NW; i += NT) tabs[i * GT] = make_float2(0.0f, 0.0f);
     __syncthreads();
     for (int j = tid; j < n_oth; j += NT) {
@@ -176,10 +179,6 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     // -- chain pairs ------------------------------------------------------------
     float2* tab0 = tabs + (2 * warp) * GT;
     float2* tab1 = tab0 + GT;
-    float accv[KMAX];
-    float accq[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) { accv[k] = 0.0f; accq[k] = 0.0f; }
     const int n_pairs = (ng + 1) >> 1;
     for (int pi = warp; pi < n_pairs; pi += NW) {
         const int ch0 = r0 + 2 * pi;
@@ -276,8 +275,11 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
             }
             if (accum) {
                 const float p0 = act ? o0.phi : 0.0f, p1 = act1 ? o1.phi : 0.0f;
-                accv[k] += p0 + p1;
-                if (accum2) accq[k] = fmaf(p0, p0, fmaf(p1, p1, accq[k]));
+                // one shared-memory add per site and pair of realisations
+                if (act) {
+                    atomicAdd(acc_s + j, p0 + p1);
+                    if (accum2) atomicAdd(acc_s + NMAX + j, fmaf(p0, p0, p1 * p1));
+                }
             }
         }
         cnt0 = warp_sum(cnt0);
@@ -298,14 +300,6 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         __syncwarp();  // the tables are refilled by the next pair
     }
     if (accum) {
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            const int j = lane + k * 32;
-            if (j < n_own) {
-                atomicAdd(acc_s + j, accv[k]);
-                if (accum2) atomicAdd(acc_s + NMAX + j, accq[k]);
-            }
-        }
         __syncthreads();
         const bool shared_slots = gridDim.y > 1;
         double* acc1 = a.acc1 + I.slot_off + off_own;
@@ -423,13 +417,13 @@ __global__ void tile_halo_kernel(const ImgDev* img, TileDesc* tiles, const int* 
     }
 }
 
-template <int TX, int TY, int NW, int K>
-cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
+template <int TX, int TY, int NW, int K, bool ACC>
+cudaError_t launch_one(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
     using Cfg = TiledCfg<TX, TY, NW>;
     static_assert(Cfg::smem_max <= 227 * 1024, "shared memory");
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tiled_pass_kernel<TX, TY, NW, K>,
+        cudaError_t e = cudaFuncSetAttribute(tiled_pass_kernel<TX, TY, NW, K, ACC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Cfg::smem_max);
         if (e != cudaSuccess) return e;
@@ -438,8 +432,18 @@ cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s, bool set
     if (setup_only) return cudaSuccess;
     if (a.gt < 1 || a.gt > Cfg::GT) return cudaErrorInvalidValue;
     dim3 grid(n_tiles, (a.n_chains + a.chain_group - 1) / a.chain_group);
-    tiled_pass_kernel<TX, TY, NW, K><<<grid, Cfg::NT, Cfg::smem_for(a.gt), s>>>(a);
+    tiled_pass_kernel<TX, TY, NW, K, ACC><<<grid, Cfg::NT, Cfg::smem_for(a.gt), s>>>(a);
     return cudaGetLastError();
+}
+
+template <int TX, int TY, int NW, int K>
+cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
+    if (setup_only) {
+        cudaError_t e = launch_one<TX, TY, NW, K, false>(a, n_tiles, s, true);
+        return e != cudaSuccess ? e : launch_one<TX, TY, NW, K, true>(a, n_tiles, s, true);
+    }
+    if (a.flags & kAccumulate) return launch_one<TX, TY, NW, K, true>(a, n_tiles, s, false);
+    return launch_one<TX, TY, NW, K, false>(a, n_tiles, s, false);
 }
 
 }  // namespace
