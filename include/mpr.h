@@ -80,7 +80,7 @@ typedef struct {
     int path;                /* mpr_path                                                       */
     int tile_x, tile_y;      /* tiled path tile shape; 0 = autotuned                          */
     int chain_group;         /* tiled path: chains per thread block, even or >= n_chains;
-                                0 = automatic                                                  */
+                                values above 32 act as 32; 0 = automatic                       */
     int literal_or;          /* 1: over-relaxation as printed in Eq. over-relax (q = 1 field,
                                 always applied), for comparison; plain path only; 0           */
     int use_graphs;          /* 1: runs of 4 or more sweeps on a non-default stream are captured
@@ -142,7 +142,7 @@ mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly,
 /* Autotuner of the tiled path: times `sweeps` equilibration sweeps of the
  * given batch (after one warm-up sweep, temperature from the harmonic guess
  * 4 (e_s + J)) for each candidate tile shape (32x16, 16x16, 32x32) and chain
- * group (automatic, 8, 2) that fits `workspace`, and writes the fastest into
+ * group (automatic, 16, 8) that fits `workspace`, and writes the fastest into
  * p->tile_x, tile_y, chain_group.  timings (nullable, host [9]) receives
  * milliseconds per sweep, tile-major, -1 for skipped candidates.  The
  * workspace is scratch here (size it with mpr_workspace_size for 16x16

@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmpr.so")
-SOURCES = ["mpr_api.cu", "mpr_tiled.cu", "mpr_plain.cu", "mpr_lattice.cu", "mpr_noalloc.cu"]
-HEADERS = ["mpr_device.cuh", "mpr_internal.h", "mpr_async.cuh"]
+SOURCES = ["mpr_api.cu", "mpr_tiled.cu", "mpr_tiled_32x16.cu", "mpr_tiled_16x16.cu",
+           "mpr_tiled_32x32.cu", "mpr_plain.cu", "mpr_lattice.cu", "mpr_noalloc.cu"]
+HEADERS = ["mpr_device.cuh", "mpr_internal.h", "mpr_async.cuh", "mpr_tiled_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr"]

@@ -48,7 +48,7 @@ constexpr double kPiD = 3.14159265358979323846;
 struct Layout {
     size_t img, ctl, ch_a, ch_cnt, ch_last, ch_ecur, ch_elast, ch_esum, ch_esum2;
     size_t zst, gst, outst, eout, samp, slot_map, tiles, counts, halo, scratch;
-    size_t slot_pos, acc1, acc2, state, newton, hist, sub;
+    size_t slot_pos, slot_ref, slot_cs, acc1, acc2, state, newton, hist, sub;
     size_t total;
     long long n_slots;   // slot space over all images
     long long n_state;   // floats of the state buffer
@@ -63,6 +63,12 @@ struct Geometry {
     int n_tiles = 0;
     int max_Lx = 0, max_Ly = 0;
 };
+
+// Floats per slot of the state buffer: the tiled layout interleaves the
+// chains, rounded up to an even count so that chain pairs are aligned float2.
+long long state_chains(const Geometry& g) {
+    return g.path == MPR_PATH_TILED ? (long long)((g.n_chains + 1) & ~1) : (long long)g.n_chains;
+}
 
 void make_geometry(Geometry& g, int n_img, const int* Lx, const int* Ly, int n_chains, int path,
                    int tx, int ty) {
@@ -124,9 +130,11 @@ Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_im
     L.n_state = 0;
     for (int i = 0; i < g.n_img; ++i) {
         L.n_slots += slots_per_img[i];
-        L.n_state += slots_per_img[i] * g.n_chains;
+        L.n_state += slots_per_img[i] * state_chains(g);
     }
     L.slot_pos = take(tiled ? sizeof(uint32_t) * L.n_slots : 0);
+    L.slot_ref = take(tiled ? sizeof(uint2) * L.n_slots : 0);
+    L.slot_cs = take(tiled ? sizeof(float2) * L.n_slots : 0);
     L.acc1 = take(sizeof(double) * L.n_slots);
     L.acc2 = take(sizeof(double) * L.n_slots);
     L.state = take(sizeof(float) * L.n_state);
@@ -170,6 +178,8 @@ struct mpr_ctx {
     TileDesc* d_tiles = nullptr;
     int2* d_halo = nullptr;
     uint32_t* d_slot_pos = nullptr;
+    uint2* d_slot_ref = nullptr;
+    float2* d_slot_cs = nullptr;
     double* d_acc1 = nullptr;
     double* d_acc2 = nullptr;
     float* d_state = nullptr;
@@ -183,8 +193,7 @@ struct mpr_ctx {
     // host mirrors
     std::vector<ImgDev> h_img;
     std::vector<long long> slots;
-    int gt[2] = {1, 1};           // tiled: per-warp table entries for the pass of colour c
-    int kload[2] = {1, 1};        // tiled: largest colour count of the pass's tiles / 32
+    int gt[2] = {1, 1};           // tiled: table entries for the pass of colour c
     uint32_t sweep = 0, equil_index = 0;
     long long n_meas_done = 0;
     bool T_set = false;
@@ -223,6 +232,8 @@ void bind_views(mpr_ctx* c) {
     c->d_tiles = at<TileDesc>(w, L.tiles);
     c->d_halo = at<int2>(w, L.halo);
     c->d_slot_pos = at<uint32_t>(w, L.slot_pos);
+    c->d_slot_ref = at<uint2>(w, L.slot_ref);
+    c->d_slot_cs = at<float2>(w, L.slot_cs);
     c->d_acc1 = at<double>(w, L.acc1);
     c->d_acc2 = at<double>(w, L.acc2);
     c->d_state = at<float>(w, L.state);
@@ -311,19 +322,21 @@ __global__ void sample_energy_kernel(const ImgDev* img, const float* samp, doubl
 }
 
 // Start of the tiled state: hot (slot -> 2 pi u with the site's first uniform
-// at sweep 0xFFFFFFFF) or cold (every gap angle pi); padding slots hold 0.
+// at sweep 0xFFFFFFFF) or cold (every gap angle pi); padding slots and the
+// padding chain of an odd chain count hold 0.
 __global__ void hot_start_tiled_kernel(const ImgDev* img, const uint32_t* slot_pos, float* state,
                                        long long slots_img, int img_i, int n_chains, uint2 key,
                                        uint32_t img_tag, int cold) {
     const ImgDev& I = img[img_i];
-    const long long total = slots_img * n_chains;
+    const long long cp = I.sstride;
+    const long long total = slots_img * cp;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const int chain = (int)(t / slots_img);
-        const long long k = t - (long long)chain * slots_img;
+        const long long k = t / cp;
+        const int chain = (int)(t - k * cp);
         const uint32_t p = slot_pos[I.slot_off + k];
         float v = 0.0f;
-        if (p != 0xFFFFFFFFu) {
+        if (p != 0xFFFFFFFFu && chain < n_chains) {
             if (cold) {
                 v = kPi;
             } else {
@@ -334,7 +347,7 @@ __global__ void hot_start_tiled_kernel(const ImgDev* img, const uint32_t* slot_p
                 v = kTwoPi * u24(wu);
             }
         }
-        state[I.state_off + (long long)chain * I.stride + k] = v;
+        state[state_index(I, chain, k)] = v;
     }
 }
 
@@ -360,7 +373,7 @@ __global__ void init_plain_kernel(const ImgDev* img, const float* samp, float* s
                                (uint32_t)img_i | img_tag, key, wu, wr);
             out = kTwoPi * u24(wu);
         }
-        state[I.state_off + (long long)chain * I.stride + i] = out;
+        state[state_index(I, chain, i)] = out;
     }
 }
 
@@ -477,12 +490,11 @@ __global__ void newton_init_kernel(ImgDev* sub_img, const ImgDev* main_img, doub
 __device__ __forceinline__ float site_value(const ImgDev& I, const float* state, const float* samp,
                                             const int* slot_map, int tiled, int chain,
                                             long long i) {
-    const float* st = state + I.state_off + (long long)chain * I.stride;
     if (tiled) {
         const int s = slot_map[I.site_off + i];
-        return s >= 0 ? st[s] : samp[I.site_off + i];
+        return s >= 0 ? state[state_index(I, chain, s)] : samp[I.site_off + i];
     }
-    return fabsf(st[i]);
+    return fabsf(state[state_index(I, chain, i)]);
 }
 
 // H of every (image, chain) (blockIdx.y), FP64 sums of FP32 bond terms.
@@ -527,14 +539,14 @@ __global__ void state_copy_kernel(const ImgDev* img, float* state, const float* 
     const ImgDev& I = img[im];
     const long long n = (long long)I.Lx * I.Ly;
     float* d = plane ? plane : dense + I.site_off * n_chains + (long long)chain * n;
-    float* st = state + I.state_off + (long long)chain * I.stride;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (tiled) {
             const int s = slot_map[I.site_off + i];
-            if (dir == 0) d[i] = s >= 0 ? st[s] : samp[I.site_off + i];
-            else if (s >= 0) st[s] = d[i];
+            if (dir == 0) d[i] = s >= 0 ? state[state_index(I, chain, s)] : samp[I.site_off + i];
+            else if (s >= 0) state[state_index(I, chain, s)] = d[i];
         } else {
+            float* st = state + state_index(I, chain, 0);
             const float v = st[i];
             if (dir == 0) d[i] = fabsf(v);
             else if (!is_fixed(v)) st[i] = d[i];
@@ -650,16 +662,18 @@ void pick_tiles(const mpr_params& p, int n_img, const int* Lx, const int* Ly, in
     ty = 16;
 }
 
+// Chains per thread block of the tiled pass (even, or covering every chain;
+// at most 32).  Automatic: the largest power of two up to 32 that still gives
+// about two waves of blocks (152 SMs x 4 blocks).
 int pick_chain_group(const mpr_ctx* c) {
-    if (c->p.chain_group > 0) return std::min(c->p.chain_group, 64);
     if (c->g.path != MPR_PATH_TILED) return 1;
-    // enough thread blocks to fill the GPU several times over
-    const long long target = 152LL * 8;
+    const int n = c->g.n_chains;
+    if (c->p.chain_group > 0) return std::min(c->p.chain_group, 32);
+    const long long target = 152LL * 4 * 2;
     const long long tiles = std::max(1, c->g.n_tiles);
-    int cg = (int)std::min<long long>(64, std::max<long long>(1, tiles * c->g.n_chains / target));
-    cg = std::min(cg, c->g.n_chains);
-    if (cg < c->g.n_chains) cg = std::max(2, cg & ~1);  // groups start at even chains
-    return std::max(cg, 1);
+    int cg = 2;
+    while (cg < 32 && cg < n && tiles * ((n + 2 * cg - 1) / (2 * cg)) >= target) cg *= 2;
+    return cg >= n ? n : cg;
 }
 
 mpr_status sub_workspace_size(const mpr_params& p, const mpr_T_opts& o, int n_img, const int* Lx,
@@ -848,20 +862,10 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
                 }
             }
             c->slots[i] = off;
-            for (int t = g.tile0[i]; t < g.tile0[i] + g.ntiles[i]; ++t)
-                for (int col = 0; col < 2; ++col) {
-                    c->gt[col] = std::max(c->gt[col], h_counts[2 * t + (col ^ 1)] + g.halo_cap + 1);
-                    const int m = std::max(h_counts[2 * t], h_counts[2 * t + 1]);
-                    c->kload[col] = std::max(c->kload[col], (m + 31) / 32);
-                }
         } else {
             c->slots[i] = (long long)Lx[i] * Ly[i];
         }
     }
-    if (tiled && std::max(c->kload[0], c->kload[1]) > tiled_max_kload(tx, ty))
-        return fail(MPR_ERR_INVALID_ARG, "tile shape " + std::to_string(tx) + "x" +
-                                             std::to_string(ty) +
-                                             " cannot serve this gap density; use 32x16");
     c->L = make_layout(g, c->slots, sub_bytes, staging);
     if (c->L.total > ws_bytes)
         return fail(MPR_ERR_WORKSPACE, "workspace too small: need " + std::to_string(c->L.total) +
@@ -872,9 +876,11 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
         ImgDev& I = c->h_img[i];
         I.slot_off = slot_off;
         I.state_off = state_off;
-        I.stride = c->slots[i];
+        // tiled: slot-major, chains interleaved; plain: one dense plane per chain
+        I.stride = tiled ? 1 : c->slots[i];
+        I.sstride = tiled ? state_chains(g) : 1;
         slot_off += c->slots[i];
-        state_off += c->slots[i] * n_chains;
+        state_off += c->slots[i] * state_chains(g);
     }
     MPR_CUDA(cudaMemcpyAsync(c->d_img, c->h_img.data(), sizeof(ImgDev) * n_img,
                              cudaMemcpyHostToDevice, s));
@@ -884,17 +890,27 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
         MPR_CUDA(cudaMemsetAsync(c->d_slot_pos, 0xFF, sizeof(uint32_t) * c->L.n_slots, s));
         MPR_CUDA(launch_tile_fill(c->d_img, c->d_tiles, g.n_tiles, d_gap, tx, ty, c->d_slot_pos,
                                   c->d_slot_map, c->d_halo, g.halo_cap, s));
+        // table size of each pass from the ring lists just built
+        int* gt = at<int>(c->ws, c->L.counts);
+        MPR_CUDA(cudaMemsetAsync(gt, 0, sizeof(int) * 2, s));
+        MPR_CUDA(launch_tile_gt(c->d_tiles, g.n_tiles, gt, s));
+        MPR_CUDA(cudaMemcpyAsync(c->gt, gt, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaStreamSynchronize(s));
     }
     long long maxn = 0;
     for (int i = 0; i < n_img; ++i) maxn = std::max(maxn, (long long)Lx[i] * Ly[i]);
     map_kernel<<<dim3(grid_for(maxn, 256, 2048), n_img), 256, 0, s>>>(c->d_img, d_z, d_gap, c->d_samp,
                                                                       unconditional ? 1 : 0);
     MPR_CUDA(cudaGetLastError());
+    if (tiled)
+        MPR_CUDA(launch_tile_const(c->d_img, c->d_tiles, g.n_tiles, tx, ty, c->d_slot_pos,
+                                   c->d_halo, g.halo_cap, c->d_samp, (float)c->p.q, c->d_slot_ref,
+                                   c->d_slot_cs, s));
     const uint2 key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
     for (int i = 0; i < n_img; ++i) {
         if (tiled) {
             // the temperature lattices start cold (see mpr_estimate_T), images hot
-            hot_start_tiled_kernel<<<grid_for(c->slots[i] * n_chains), 256, 0, s>>>(
+            hot_start_tiled_kernel<<<grid_for(c->slots[i] * state_chains(g)), 256, 0, s>>>(
                 c->d_img, c->d_slot_pos, c->d_state, c->slots[i], i, n_chains, key, c->img_tag,
                 unconditional ? 1 : 0);
         } else {
@@ -947,6 +963,8 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
     a.img = c->d_img;
     a.tiles = c->d_tiles;
     a.slot_pos = c->d_slot_pos;
+    a.slot_ref = c->d_slot_ref;
+    a.slot_cs = c->d_slot_cs;
     a.halo = c->d_halo;
     a.samp = c->d_samp;
     a.state = c->d_state;
@@ -979,8 +997,7 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
             a.colour = colour;
             a.gt = c->gt[colour];
             a.flags = base | ((record && colour == 1) ? kEnergy : 0);
-            cudaError_t e = tiled ? launch_tiled_pass(a, c->g.n_tiles, c->g.tx, c->g.ty,
-                                                      c->kload[colour], s)
+            cudaError_t e = tiled ? launch_tiled_pass(a, c->g.n_tiles, c->g.tx, c->g.ty, s)
                                   : launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
         }
@@ -1016,8 +1033,9 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
         if (!exec) {
             if (c->g.path == MPR_PATH_TILED) {
                 SweepArgs a{};
-                for (int col = 0; col < 2; ++col)
-                    MPR_CUDA(launch_tiled_pass(a, 0, c->g.tx, c->g.ty, c->kload[col], s, true));
+                a.n_chains = c->g.n_chains;
+                a.chain_group = pick_chain_group(c);
+                MPR_CUDA(launch_tiled_pass(a, 0, c->g.tx, c->g.ty, s, true));
             }
             MPR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             const mpr_status st = launch_sweeps(c, n, phase, flags, stats, accumulate, s);
@@ -1260,7 +1278,7 @@ mpr_status mpr_autotune(int n_img, const int* Lx, const int* Ly, int n_chains, m
     if (!z || !gap || sweeps < 1) return fail(MPR_ERR_INVALID_ARG, "bad arguments");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     static const int tiles[3][2] = {{32, 16}, {16, 16}, {32, 32}};
-    const int groups[3] = {0, 8, 2};
+    const int groups[3] = {0, 16, 8};
     double best = 1e300;
     int bt = -1, bg = 0;
     for (int ti = 0; ti < 3; ++ti) {

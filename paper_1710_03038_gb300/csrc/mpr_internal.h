@@ -27,8 +27,9 @@ struct TileDesc {
 struct ImgDev {
     int Lx, Ly;
     long long site_off;   // offset in concatenated [sum Lx*Ly] arrays
-    long long state_off;  // float offset of chain 0 in the state buffer
-    long long stride;     // floats between consecutive chains
+    long long state_off;  // float offset of chain 0, slot 0 in the state buffer
+    long long stride;     // floats between consecutive chains (tiled: 1)
+    long long sstride;    // floats between consecutive slots (tiled: chains rounded up to even)
     long long slot_off;   // tiled: offset in the slot arrays (acc, slot_pos); plain: site_off
     int tile0, ntiles;
     float zmin, zmax;
@@ -74,6 +75,8 @@ struct SweepArgs {
     const ImgDev* img;
     const TileDesc* tiles;      // tiled path
     const uint32_t* slot_pos;   // tiled: (y << 16) | x per slot, 0xFFFFFFFF for padding
+    const uint2* slot_ref;      // tiled: table entries of the slot's gap neighbours (u16 x 4)
+    const float2* slot_cs;      // tiled: sum over the slot's sample neighbours of (cos, sin) q phi
     const int2* halo;           // tiled: [tile][2][cap] (slot, cs index)
     const float* samp;          // tiled: sample angle per site (>= 0) or -1 at gaps
     float* state;
@@ -89,7 +92,7 @@ struct SweepArgs {
     int colour;
     int flags;
     int halo_cap;
-    int gt;                    // tiled: table entries per warp table for this pass
+    int gt;                    // tiled: table entries per chain pair for this pass
     int n_img;
     uint32_t img_tag;          // OR-ed into the image field of the counter (1 << 30: T lattices)
 };
@@ -99,11 +102,11 @@ mpr_status set_last_error(mpr_status s, const std::string& msg);
 
 // ---- launchers ------------------------------------------------------------
 // setup_only: set the kernel's attributes without launching (before a capture)
+// (chain_group: even and at most 32, or covering every chain)
 cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tile_x, int tile_y,
-                              int kload, cudaStream_t s, bool setup_only = false);
+                              cudaStream_t s, bool setup_only = false);
 cudaError_t launch_plain_pass(const SweepArgs& a, int max_Lx, int max_Ly, cudaStream_t s);
 bool tiled_config_supported(int tile_x, int tile_y);
-int tiled_max_kload(int tile_x, int tile_y);  // largest per-lane site count a tile shape serves
 
 // tile-table construction (tiled path)
 cudaError_t launch_tile_count(const ImgDev* img, const TileDesc* tiles, int n_tiles,
@@ -112,5 +115,18 @@ cudaError_t launch_tile_count(const ImgDev* img, const TileDesc* tiles, int n_ti
 cudaError_t launch_tile_fill(const ImgDev* img, const TileDesc* tiles, int n_tiles,
                              const uint8_t* gap, int tile_x, int tile_y, uint32_t* slot_pos,
                              int* slot_map, int2* halo, int halo_cap, cudaStream_t s);
+// per slot: the table entries of its gap neighbours in the pass of its own
+// colour (up, down, left, right; 0 = not a gap) and its sample field
+cudaError_t launch_tile_const(const ImgDev* img, const TileDesc* tiles, int n_tiles, int tile_x,
+                              int tile_y, const uint32_t* slot_pos, const int2* halo, int halo_cap,
+                              const float* samp, float q, uint2* slot_ref, float2* slot_cs,
+                              cudaStream_t s);
+// out[c] = table entries of the pass of colour c (out must hold zeros)
+cudaError_t launch_tile_gt(const TileDesc* tiles, int n_tiles, int* out, cudaStream_t s);
+
+// float offset of gap slot k (tiled) or site k (plain) of a realisation
+__host__ __device__ inline long long state_index(const ImgDev& I, int chain, long long k) {
+    return I.state_off + (long long)chain * I.stride + k * I.sstride;
+}
 
 }  // namespace mpr

@@ -26,7 +26,7 @@ plain_pass_kernel(SweepArgs a) {
     const int m = blockIdx.x * kPlainBX + threadIdx.x;
     const int x = 2 * m + ((y + colour) & 1);
     const bool inside = (y < I.Ly) && (x < I.Lx);
-    float* P = a.state + I.state_off + (long long)chain * I.stride;
+    float* P = a.state + state_index(I, chain, 0);
     const uint32_t sweep = a.ctl->sweep;
 
     unsigned n_acc = 0;
