@@ -654,11 +654,13 @@ void pick_tiles(const mpr_params& p, int n_img, const int* Lx, const int* Ly, in
     tx = p.tile_x;
     ty = p.tile_y;
     if (tx > 0 && ty > 0) return;
-    long long n = 0;
-    int mx = 0;
-    for (int i = 0; i < n_img; ++i) { n += (long long)Lx[i] * Ly[i]; mx = std::max(mx, std::max(Lx[i], Ly[i])); }
+    (void)n_img;
+    (void)Lx;
+    (void)Ly;
     (void)n_chains;
-    tx = 32;
+    // 16 x 16: the shortest block life per chain group of 32 (measured fastest
+    // of the three shapes on 4096^2 images at 40 % gaps)
+    tx = 16;
     ty = 16;
 }
 
