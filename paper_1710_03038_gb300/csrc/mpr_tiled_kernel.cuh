@@ -247,15 +247,11 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     if (ACC) {
         double* acc1 = a.acc1 + I.slot_off + off_own;
         double* acc2 = a.acc2 + I.slot_off + off_own;
-        const bool shared_slots = gridDim.y > 1;  // other chain groups add to the same sites
+        // fire-and-forget adds: no block waits for a read of the old sums (with
+        // one chain group per tile each address gets one add per pass)
         for (int j = tid; j < n_own; j += NT) {
-            if (shared_slots) {
-                atomicAdd(acc1 + j, (double)acc_s[j]);
-                if (accum2) atomicAdd(acc2 + j, (double)acc_s[NMAX + j]);
-            } else {
-                acc1[j] += (double)acc_s[j];
-                if (accum2) acc2[j] += (double)acc_s[NMAX + j];
-            }
+            atomicAdd(acc1 + j, (double)acc_s[j]);
+            if (accum2) atomicAdd(acc2 + j, (double)acc_s[NMAX + j]);
         }
     }
     if (tid < P && 2 * tid < ng) {
