@@ -139,6 +139,15 @@ class Context:
             gf = torch.cat([(t.reshape(-1) != 0).to(torch.uint8) for t in gs]).contiguous()
             where = _lib.MPR_DEVICE
             ng = [int(g.count_nonzero()) for g in gs]
+        elif (len(zs) == 1 and isinstance(zs[0], torch.Tensor) and isinstance(gs[0], torch.Tensor)
+              and zs[0].dtype == torch.float32 and gs[0].dtype in (torch.uint8, torch.bool)
+              and zs[0].is_contiguous() and gs[0].is_contiguous()
+              and zs[0].is_pinned() and gs[0].is_pinned()):
+            # pinned host buffers of the library's types: handed over as they are
+            zf = zs[0].reshape(-1)
+            gf = gs[0].reshape(-1).view(torch.uint8)
+            where = _lib.MPR_HOST
+            ng = [int(np.count_nonzero(gf.numpy()))]
         else:
             zn = [np.asarray(t.cpu() if isinstance(t, torch.Tensor) else t, dtype=np.float32) for t in zs]
             gn = [(np.asarray(t.cpu() if isinstance(t, torch.Tensor) else t) != 0).astype(np.uint8) for t in gs]

@@ -47,9 +47,8 @@ struct Cfg {
     static constexpr int HCAP = TX + TY;           // ring cells of one colour
     static constexpr int GT = NMAX + HCAP + 1;     // table entries (entry 0 = zeros)
     static constexpr size_t a16(size_t v) { return (v + 15) / 16 * 16; }
-    static constexpr size_t off_ref = 0;
-    static constexpr size_t off_cs = off_ref + sizeof(uint2) * NMAX;
-    static constexpr size_t off_c0 = off_cs + sizeof(float2) * NMAX;
+    static constexpr size_t off_rc = 0;  // per own site: neighbour rows, sample field
+    static constexpr size_t off_c0 = off_rc + sizeof(uint4) * NMAX;
     static constexpr size_t off_acc = off_c0 + sizeof(uint32_t) * NMAX;  // [2][NMAX] site sums
     static constexpr size_t off_red = a16(off_acc + sizeof(float) * 2 * NMAX);
     // the table last, sized at launch for the largest tile of the pass
@@ -67,8 +66,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     constexpr int SPW = 32 / P;  // sites per warp step
     static_assert(P >= 1 && P <= 16 && (P & (P - 1)) == 0, "pairs per site: power of two");
     extern __shared__ __align__(16) unsigned char smem[];
-    uint2* own_ref = reinterpret_cast<uint2*>(smem + C::off_ref);
-    float2* own_cs = reinterpret_cast<float2*>(smem + C::off_cs);
+    uint4* own_rc = reinterpret_cast<uint4*>(smem + C::off_rc);
     uint32_t* own_c0 = reinterpret_cast<uint32_t*>(smem + C::off_c0);
     float* acc_s = reinterpret_cast<float*>(smem + C::off_acc);
     float4* red = reinterpret_cast<float4*>(smem + C::off_red);
@@ -113,9 +111,10 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         for (int j = tid; j < n_own; j += NT) {
             const uint2 r = a.slot_ref[b + j];
             // table rows (entry * P) of the four neighbours, for the gathers
-            own_ref[j] = make_uint2(((r.x & 0xFFFFu) * P) | (((r.x >> 16) * P) << 16),
-                                    ((r.y & 0xFFFFu) * P) | (((r.y >> 16) * P) << 16));
-            own_cs[j] = a.slot_cs[b + j];
+            const float2 f = a.slot_cs[b + j];
+            own_rc[j] = make_uint4(((r.x & 0xFFFFu) * P) | (((r.x >> 16) * P) << 16),
+                                   ((r.y & 0xFFFFu) * P) | (((r.y >> 16) * P) << 16),
+                                   __float_as_uint(f.x), __float_as_uint(f.y));
             const uint32_t pos = a.slot_pos[b + j];
             own_c0[j] = (pos & 0xFFFF0000u) | ((pos & 0xFFFFu) >> 1);
         }
@@ -169,13 +168,15 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
                              : kTwoPi / a.ch.a[t_img * a.n_chains + r0 + 2 * p + 1];
     unsigned cnt0 = 0, cnt1 = 0;
     const int n_steps = (n_own + SPW - 1) / SPW;
+    float* sto = st + (long long)off_own * cp;  // this lane's pair at the own segment
+    const int cpi = (int)cp;
     for (int g0 = warp; g0 < n_steps; g0 += U * NW) {  // warp-uniform
         float2 v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = (g0 + u * NW) * SPW + s;
             v[u] = make_float2(0.0f, 0.0f);
-            if (has0 && j < n_own) v[u] = *reinterpret_cast<const float2*>(st + (long long)(off_own + j) * cp);
+            if (has0 && j < n_own) v[u] = *reinterpret_cast<const float2*>(sto + j * cpi);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -185,8 +186,9 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
             const bool in = j < n_own;
             const bool act = in && has0;
             const int jj = in ? j : 0;  // idle lanes recompute slot 0 and store nothing
-            const uint2 rf = own_ref[jj];
-            const float2 fs = own_cs[jj];
+            const uint4 rc = own_rc[jj];
+            const uint2 rf = make_uint2(rc.x, rc.y);
+            const float2 fs = make_float2(__uint_as_float(rc.z), __uint_as_float(rc.w));
             const uint4 w = philox4x32_10_rk(make_uint4(own_c0[jj], sweep, c2, c3), a.rk);
             const float4 gu = tab[(rf.x & 0xFFFFu) + p], gd = tab[(rf.x >> 16) + p];
             const float4 gl = tab[(rf.y & 0xFFFFu) + p], gr = tab[(rf.y >> 16) + p];
@@ -198,7 +200,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
             const UpdateOut o1 = hybrid_update(v[u].y, C1, S1, w.z, w.w, uk, alpha1, invT);
             const bool act1 = act && has1;
             // a missing second chain is the padding chain of the layout: storing there is harmless
-            if (act) *reinterpret_cast<float2*>(st + (long long)(off_own + j) * cp) = make_float2(o0.phi, o1.phi);
+            if (act) *reinterpret_cast<float2*>(sto + j * cpi) = make_float2(o0.phi, o1.phi);
             cnt0 += (act && o0.accepted) ? 1u : 0u;
             cnt1 += (act1 && o1.accepted) ? 1u : 0u;
             if (energy) {
