@@ -57,8 +57,7 @@ struct Cfg {
     static constexpr size_t smem_max = smem_for(GT, 16);
 };
 
-// U: warp steps whose state loads are issued together.
-template <int TX, int TY, int NW, int P, bool ACC, int U>
+template <int TX, int TY, int NW, int P, bool ACC>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))  // 64 registers: 32 warps per SM
 tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     using C = Cfg<TX, TY, NW>;
@@ -127,7 +126,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         const int n_ent = n_oth + n_halo;
         const int2* hl = a.halo + ((long long)blockIdx.x * 2 + c) * a.halo_cap;  // ring list
         const float2* fcs = a.slot_cs + I.slot_off + off_oth;
-        constexpr int FU = 4;  // loads issued together
+        constexpr int FU = 8;  // loads issued together
         for (int e00 = tid / P; e00 < n_ent; e00 += FU * (NT / P)) {
             float2 v[FU], f[FU];
 #pragma unroll
@@ -170,18 +169,20 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const int n_steps = (n_own + SPW - 1) / SPW;
     float* sto = st + (long long)off_own * cp;  // this lane's pair at the own segment
     const int cpi = (int)cp;
-    for (int g0 = warp; g0 < n_steps; g0 += U * NW) {  // warp-uniform
-        float2 v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = (g0 + u * NW) * SPW + s;
-            v[u] = make_float2(0.0f, 0.0f);
-            if (has0 && j < n_own) v[u] = *reinterpret_cast<const float2*>(sto + j * cpi);
+    // angles of a warp step: loaded one step ahead, in flight during the step before
+    float2 vn = make_float2(0.0f, 0.0f);
+    {
+        const int j = warp * SPW + s;
+        if (has0 && j < n_own) vn = *reinterpret_cast<const float2*>(sto + j * cpi);
+    }
+    for (int g = warp; g < n_steps; g += NW) {  // warp-uniform
+        const float2 vc = vn;
+        {
+            const int jn = (g + NW) * SPW + s;
+            vn = make_float2(0.0f, 0.0f);
+            if (has0 && jn < n_own) vn = *reinterpret_cast<const float2*>(sto + jn * cpi);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int g = g0 + u * NW;
-            if (g >= n_steps) break;  // warp-uniform
+        {
             const int j = g * SPW + s;
             const bool in = j < n_own;
             const bool act = in && has0;
@@ -196,8 +197,8 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
             const float S0 = (((fs.y + gu.y) + gd.y) + gl.y) + gr.y;
             const float C1 = (((fs.x + gu.z) + gd.z) + gl.z) + gr.z;
             const float S1 = (((fs.y + gu.w) + gd.w) + gl.w) + gr.w;
-            const UpdateOut o0 = hybrid_update(v[u].x, C0, S0, w.x, w.y, uk, alpha0, invT);
-            const UpdateOut o1 = hybrid_update(v[u].y, C1, S1, w.z, w.w, uk, alpha1, invT);
+            const UpdateOut o0 = hybrid_update(vc.x, C0, S0, w.x, w.y, uk, alpha0, invT);
+            const UpdateOut o1 = hybrid_update(vc.y, C1, S1, w.z, w.w, uk, alpha1, invT);
             const bool act1 = act && has1;
             // a missing second chain is the padding chain of the layout: storing there is harmless
             if (act) *reinterpret_cast<float2*>(sto + j * cpi) = make_float2(o0.phi, o1.phi);
@@ -281,10 +282,9 @@ template <int TX, int TY, int NW, int P, bool ACC>
 cudaError_t launch_one(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
     using C = Cfg<TX, TY, NW>;
     static_assert(C::smem_max <= 227 * 1024, "shared memory");
-    constexpr int U = 2;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tiled_pass_kernel<TX, TY, NW, P, ACC, U>,
+        cudaError_t e = cudaFuncSetAttribute(tiled_pass_kernel<TX, TY, NW, P, ACC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::smem_max);
         if (e != cudaSuccess) return e;
@@ -293,7 +293,7 @@ cudaError_t launch_one(const SweepArgs& a, int n_tiles, cudaStream_t s, bool set
     if (setup_only) return cudaSuccess;
     if (a.gt < 1 || a.gt > C::GT) return cudaErrorInvalidValue;
     dim3 grid(n_tiles, (a.n_chains + a.chain_group - 1) / a.chain_group);
-    tiled_pass_kernel<TX, TY, NW, P, ACC, U><<<grid, C::NT, C::smem_for(a.gt, P), s>>>(a);
+    tiled_pass_kernel<TX, TY, NW, P, ACC><<<grid, C::NT, C::smem_for(a.gt, P), s>>>(a);
     return cudaGetLastError();
 }
 
