@@ -1,5 +1,6 @@
-// Bulk asynchronous copies (the TMA unit's 1-D form) and shared-memory
-// mbarriers, as inline PTX for sm_90 and later.
+// Asynchronous global -> shared copies (per-thread cp.async, and the TMA
+// unit's 1-D bulk form with shared-memory mbarriers), as inline PTX for
+// sm_90 and later.
 #pragma once
 
 #include <cstdint>
@@ -9,6 +10,17 @@ namespace mpr {
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Per-thread 8-byte copy global -> shared (both addresses 8-byte aligned);
+// complete for the issuing thread once it has passed cp_async_wait_all().
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {

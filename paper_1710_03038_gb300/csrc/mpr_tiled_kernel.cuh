@@ -19,8 +19,9 @@
 //    cells (interior segment, then the 1-cell ring; entry 0 holds zeros for
 //    neighbours that are not gaps);
 //  - fills that table for all chains of the group: entry e, pair p holds
-//    (cos, sin) of q phi for both chains of the pair (one float4), loaded with
-//    float2 reads that are contiguous across the pairs of a slot;
+//    (cos, sin) of q phi for both chains of the pair (one float4); the angle
+//    pairs arrive by asynchronous 8-byte copies (cp.async) that are contiguous
+//    across the pairs of a slot, and are converted in place;
 //  - updates every own-colour gap site of every chain with Alg. 1, one Philox
 //    block serving the site in both chains of a pair (words 0-1 and 2-3), and
 //    stores the new pair as one float2.
@@ -34,6 +35,7 @@
 // the constant field of its sample neighbours).
 #pragma once
 
+#include "mpr_async.cuh"
 #include "mpr_device.cuh"
 #include "mpr_internal.h"
 
@@ -104,6 +106,19 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     float* st = a.state + I.state_off + r0 + 2 * p;
     const int spread = blockIdx.x & (kSpread - 1);
 
+    // -- table of the other colour, raw: entry 1 + e, pair p ----------------------
+    // Each thread copies the angle pairs of its entries e = tid / P (mod NT / P)
+    // straight into the first half of their table slots (all copies in flight
+    // at once, no registers) and converts the same entries below, so its own
+    // wait is enough.
+    constexpr int NTP = NT / P;
+    const int n_ent = n_oth + n_halo;
+    const int e_lo = tid / P;
+    if (has0)
+        for (int e = e_lo; e < n_oth; e += NTP)
+            cp_async8(tab + (1 + e) * P + p, st + (long long)(off_oth + e) * cp);
+    if (tid < P) tab[tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+
     // -- own-colour constants of the tile (built once per batch) ---------------
     {
         const long long b = I.slot_off + off_own;
@@ -118,41 +133,31 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
             own_c0[j] = (pos & 0xFFFF0000u) | ((pos & 0xFFFFu) >> 1);
         }
     }
-    if (tid < P) tab[tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // ring cells (slots from the ring list), same entry residue as above
+    if (has0) {
+        const int2* hl = a.halo + ((long long)blockIdx.x * 2 + c) * a.halo_cap;
+        const int e_first = e_lo + (max(n_oth - e_lo, 0) + NTP - 1) / NTP * NTP;
+        for (int e = e_first; e < n_ent; e += NTP)
+            cp_async8(tab + (1 + e) * P + p, st + (long long)hl[e - n_oth].x * cp);
+    }
+    cp_async_wait_all();
 
-    // -- table of the other colour: entry 1 + e, pair p -------------------------
+    // -- (cos, sin) of q phi in place -------------------------------------------
     float e0 = 0.0f, e1 = 0.0f;
     {
-        const int n_ent = n_oth + n_halo;
-        const int2* hl = a.halo + ((long long)blockIdx.x * 2 + c) * a.halo_cap;  // ring list
         const float2* fcs = a.slot_cs + I.slot_off + off_oth;
-        constexpr int FU = 8;  // loads issued together
-        for (int e00 = tid / P; e00 < n_ent; e00 += FU * (NT / P)) {
-            float2 v[FU], f[FU];
-#pragma unroll
-            for (int u = 0; u < FU; ++u) {
-                const int e = e00 + u * (NT / P);
-                v[u] = make_float2(0.0f, 0.0f);
-                f[u] = make_float2(0.0f, 0.0f);
-                if (has0 && e < n_ent) {
-                    const long long slot = e < n_oth ? (long long)(off_oth + e) : (long long)hl[e - n_oth].x;
-                    v[u] = *reinterpret_cast<const float2*>(st + slot * cp);
-                    if (energy && e < n_oth) f[u] = fcs[e];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < FU; ++u) {
-                const int e = e00 + u * (NT / P);
-                if (e >= n_ent) break;
-                float s0, c0, s1, c1;
-                __sincosf(a.q * v[u].x, &s0, &c0);
-                __sincosf(a.q * v[u].y, &s1, &c1);
-                tab[(1 + e) * P + p] = make_float4(c0, s0, c1, s1);
-                // bonds between this other-colour gap site and its sample neighbours
-                if (energy && e < n_oth && has0) {
-                    e0 -= a.J * fmaf(f[u].x, c0, f[u].y * s0);
-                    if (has1) e1 -= a.J * fmaf(f[u].x, c1, f[u].y * s1);
-                }
+        for (int e = e_lo; e < n_ent; e += NTP) {
+            float4* t = tab + (1 + e) * P + p;
+            const float2 v = has0 ? *reinterpret_cast<const float2*>(t) : make_float2(0.0f, 0.0f);
+            float s0, c0, s1, c1;
+            __sincosf(a.q * v.x, &s0, &c0);
+            __sincosf(a.q * v.y, &s1, &c1);
+            *t = make_float4(c0, s0, c1, s1);
+            // bonds between this other-colour gap site and its sample neighbours
+            if (energy && e < n_oth && has0) {
+                const float2 f = fcs[e];
+                e0 -= a.J * fmaf(f.x, c0, f.y * s0);
+                if (has1) e1 -= a.J * fmaf(f.x, c1, f.y * s1);
             }
         }
     }
