@@ -323,31 +323,32 @@ __global__ void sample_energy_kernel(const ImgDev* img, const float* samp, doubl
 
 // Start of the tiled state: hot (slot -> 2 pi u with the site's first uniform
 // at sweep 0xFFFFFFFF) or cold (every gap angle pi); padding slots and the
-// padding chain of an odd chain count hold 0.
+// padding chain of an odd chain count hold 0.  One thread per (slot, chain
+// pair): the pair shares its Philox block (words 0 and 2) and one float2 store.
 __global__ void hot_start_tiled_kernel(const ImgDev* img, const uint32_t* slot_pos, float* state,
                                        long long slots_img, int img_i, int n_chains, uint2 key,
                                        uint32_t img_tag, int cold) {
     const ImgDev& I = img[img_i];
-    const long long cp = I.sstride;
-    const long long total = slots_img * cp;
+    const long long np = I.sstride / 2;  // chain pairs per slot
+    const long long total = slots_img * np;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const long long k = t / cp;
-        const int chain = (int)(t - k * cp);
+        const long long k = t / np;
+        const int c0 = 2 * (int)(t - k * np);
         const uint32_t p = slot_pos[I.slot_off + k];
-        float v = 0.0f;
-        if (p != 0xFFFFFFFFu && chain < n_chains) {
+        float2 v = make_float2(0.0f, 0.0f);
+        if (p != 0xFFFFFFFFu) {
             if (cold) {
-                v = kPi;
+                v = make_float2(kPi, c0 + 1 < n_chains ? kPi : 0.0f);
             } else {
                 const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
-                uint32_t wu, wr;
-                site_uniform_words(X, Y, (X + Y) & 1, 0xFFFFFFFFu, (uint32_t)chain,
-                                   (uint32_t)img_i | img_tag, key, wu, wr);
-                v = kTwoPi * u24(wu);
+                const uint4 w = philox4x32_10(site_counter(X, Y, (X + Y) & 1, 0xFFFFFFFFu,
+                                                           (uint32_t)c0, (uint32_t)img_i | img_tag),
+                                              key);
+                v = make_float2(kTwoPi * u24(w.x), c0 + 1 < n_chains ? kTwoPi * u24(w.z) : 0.0f);
             }
         }
-        state[state_index(I, chain, k)] = v;
+        *reinterpret_cast<float2*>(state + state_index(I, c0, k)) = v;
     }
 }
 
@@ -912,7 +913,7 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
     for (int i = 0; i < n_img; ++i) {
         if (tiled) {
             // the temperature lattices start cold (see mpr_estimate_T), images hot
-            hot_start_tiled_kernel<<<grid_for(c->slots[i] * state_chains(g)), 256, 0, s>>>(
+            hot_start_tiled_kernel<<<grid_for(c->slots[i] * state_chains(g) / 2), 256, 0, s>>>(
                 c->d_img, c->d_slot_pos, c->d_state, c->slots[i], i, n_chains, key, c->img_tag,
                 unconditional ? 1 : 0);
         } else {

@@ -19,6 +19,11 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
                  : "memory");
 }
 
+// The same with the destination as a shared-window address (from smem_addr).
+__device__ __forceinline__ void cp_async8_s(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }

@@ -111,12 +111,19 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     // straight into the first half of their table slots (all copies in flight
     // at once, no registers) and converts the same entries below, so its own
     // wait is enough.
+    // Lanes without a pair copy nothing (their table column is never stored from).
     constexpr int NTP = NT / P;
     const int n_ent = n_oth + n_halo;
     const int e_lo = tid / P;
-    if (has0)
-        for (int e = e_lo; e < n_oth; e += NTP)
-            cp_async8(tab + (1 + e) * P + p, st + (long long)(off_oth + e) * cp);
+    float4* const tab_lo = tab + (1 + e_lo) * P + p;  // this thread's first entry
+    constexpr uint32_t kDstStep = sizeof(float4) * NTP * P;
+    if (has0) {
+        const float* src = st + (long long)(off_oth + e_lo) * cp;
+        const long long src_step = (long long)NTP * cp;
+        uint32_t dst = smem_addr(tab_lo);
+        for (int e = e_lo; e < n_oth; e += NTP, src += src_step, dst += kDstStep)
+            cp_async8_s(dst, src);
+    }
     if (tid < P) tab[tid] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 
     // -- own-colour constants of the tile (built once per batch) ---------------
@@ -135,26 +142,28 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     }
     // ring cells (slots from the ring list), same entry residue as above
     if (has0) {
-        const int2* hl = a.halo + ((long long)blockIdx.x * 2 + c) * a.halo_cap;
-        const int e_first = e_lo + (max(n_oth - e_lo, 0) + NTP - 1) / NTP * NTP;
-        for (int e = e_first; e < n_ent; e += NTP)
-            cp_async8(tab + (1 + e) * P + p, st + (long long)hl[e - n_oth].x * cp);
+        const int k_first = (max(n_oth - e_lo, 0) + NTP - 1) / NTP;  // steps to the ring
+        const int e_first = e_lo + k_first * NTP;
+        const int2* h = a.halo + ((long long)blockIdx.x * 2 + c) * a.halo_cap + (e_first - n_oth);
+        uint32_t dst = smem_addr(tab_lo) + (uint32_t)k_first * kDstStep;
+        for (int e = e_first; e < n_ent; e += NTP, h += NTP, dst += kDstStep)
+            cp_async8_s(dst, st + (long long)h->x * cp);
     }
     cp_async_wait_all();
 
     // -- (cos, sin) of q phi in place -------------------------------------------
     float e0 = 0.0f, e1 = 0.0f;
-    {
+    if (has0) {
         const float2* fcs = a.slot_cs + I.slot_off + off_oth;
-        for (int e = e_lo; e < n_ent; e += NTP) {
-            float4* t = tab + (1 + e) * P + p;
-            const float2 v = has0 ? *reinterpret_cast<const float2*>(t) : make_float2(0.0f, 0.0f);
+        float4* t = tab_lo;
+        for (int e = e_lo; e < n_ent; e += NTP, t += NTP * P) {
+            const float2 v = *reinterpret_cast<const float2*>(t);
             float s0, c0, s1, c1;
             __sincosf(a.q * v.x, &s0, &c0);
             __sincosf(a.q * v.y, &s1, &c1);
             *t = make_float4(c0, s0, c1, s1);
             // bonds between this other-colour gap site and its sample neighbours
-            if (energy && e < n_oth && has0) {
+            if (energy && e < n_oth) {
                 const float2 f = fcs[e];
                 e0 -= a.J * fmaf(f.x, c0, f.y * s0);
                 if (has1) e1 -= a.J * fmaf(f.x, c1, f.y * s1);
