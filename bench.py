@@ -42,6 +42,35 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# Sources that determine the colour-pass kernel; the DRAM traffic recorded
+# from an ncu capture applies only while their hash is the recorded one.
+KERNEL_SOURCES = ("mpr_tiled_kernel.cuh", "mpr_device.cuh", "mpr_async.cuh", "mpr_internal.h")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tiled_pass_kernel_lognormal2048.md")
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1710_03038_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic_per_update():
+    """DRAM bytes per gap site-update of the sampling colour pass from the committed ncu
+    summary, or None when the kernel sources changed since that capture."""
+    import re
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    with open(TRAFFIC_PROFILE) as f:
+        m = re.search(r"traffic record: ([0-9.]+) B per gap site-update, kernel sources ([0-9a-f]+)",
+                      f.read())
+    if not m or m.group(2) != kernel_sources_hash():
+        return None
+    return float(m.group(1))
+
+
 def max_over_ranks(values, device):
     """Element-wise maximum of per-rank timings over all ranks (identity on one rank)."""
     import torch
@@ -274,6 +303,10 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     alg_bytes_per_update = 4.0 * (1.0 / f + 1.0)
     achieved = (P * R / 2.0) * alg_bytes_per_update / (launch_ms / 1e3) / 1e9
+    # ncu DRAM bytes of one sampling launch, captured at 2048^2 and scaled by the
+    # updates of one 4096^2 launch (the pass moves a fixed amount per update)
+    tpu = recorded_traffic_per_update() if args.path == "tiled" else None
+    traffic = None if tpu is None else tpu * P * R / 2.0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -286,7 +319,7 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (state 2.1 GB)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "tiled_pass_kernel" if args.path == "tiled" else "plain_pass_kernel",
                      "alg_bytes_per_gap_update": alg_bytes_per_update,
                      "avg_launch_ms": launch_ms, "peak_kind": peak_kind},
