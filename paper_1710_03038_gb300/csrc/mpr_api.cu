@@ -667,13 +667,14 @@ void pick_tiles(const mpr_params& p, int n_img, const int* Lx, const int* Ly, in
 
 // Chains per thread block of the tiled pass (even, or covering every chain;
 // at most 32).  Automatic: the largest power of two up to 32 that still gives
-// at least three blocks per SM (152 SMs); on the 256^2 x 16 temperature
-// lattices that is 4 (measured 7.3 ms per estimate against 9.3 ms with 2).
+// at least four blocks per SM (152 SMs); on the 256^2 x 16 temperature
+// lattices that is 4 (measured 7.3 ms per estimate against 9.3 ms with 2 and
+// 7.5 ms with 8).
 int pick_chain_group(const mpr_ctx* c) {
     if (c->g.path != MPR_PATH_TILED) return 1;
     const int n = c->g.n_chains;
     if (c->p.chain_group > 0) return std::min(c->p.chain_group, 32);
-    const long long target = 152LL * 3;
+    const long long target = 152LL * 4;
     const long long tiles = std::max(1, c->g.n_tiles);
     int cg = 2;
     while (cg < 32 && cg < n && tiles * ((n + 2 * cg - 1) / (2 * cg)) >= target) cg *= 2;
