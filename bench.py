@@ -229,6 +229,7 @@ def run_gpu(args):
     torch.cuda.set_stream(stream)
 
     sweep_events = []
+    equil_events = []
 
     def step(z_in, g_in, host_out=None, timed=False):
         ctx = mpr.Context([z_in], [g_in], chains=R, params=params, topts=topts, device=dev)
@@ -236,7 +237,15 @@ def run_gpu(args):
             ctx.estimate_T_async()
         else:
             ctx.set_T([args.T])
-        ctx.sweep(ne, "equil")
+        if timed:
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            ctx.sweep(ne, "equil")
+            q1.record(stream)
+            equil_events.append((q0, q1))
+        else:
+            ctx.sweep(ne, "equil")
         if timed:
             for _ in range(nm):
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -299,6 +308,7 @@ def run_gpu(args):
     value = job_throughput(units_step, args.steps, ws, ms)
     e2e = job_throughput(units_step, args.steps, ws, ms_e2e)
     sweep_ms = [a.elapsed_time(b) for a, b in sweep_events]
+    equil_ms = [a.elapsed_time(b) / ne for a, b in equil_events]
     launch_ms = statistics.mean(sweep_ms) / 2.0  # two colour passes per sweep
     peak, peak_kind = _peaks()
     alg_bytes_per_update = 4.0 * (1.0 / f + 1.0)
@@ -323,6 +333,10 @@ def run_gpu(args):
                      "kernel": "tiled_pass_kernel" if args.path == "tiled" else "plain_pass_kernel",
                      "alg_bytes_per_gap_update": alg_bytes_per_update,
                      "avg_launch_ms": launch_ms, "peak_kind": peak_kind},
+        # gap site-updates/s of the sweeps alone, by phase (equilibration: the run of
+        # sweeps as one graph replay; measurement: events around each sweep)
+        "phases": {"equil": P * R / (statistics.mean(equil_ms) / 1e3),
+                   "measure": P * R / (statistics.mean(sweep_ms) / 1e3), "unit": UNIT},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N * 5,
                 "d2h_bytes_per_step": N * 4},
         "clocks": clocks,

@@ -1,6 +1,5 @@
-// Asynchronous global -> shared copies (per-thread cp.async, and the TMA
-// unit's 1-D bulk form with shared-memory mbarriers), as inline PTX for
-// sm_90 and later.
+// Asynchronous global -> shared copies (per-thread cp.async), as inline PTX
+// for sm_80 and later.
 #pragma once
 
 #include <cstdint>
@@ -12,74 +11,15 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Per-thread 8-byte copy global -> shared (both addresses 8-byte aligned);
-// complete for the issuing thread once it has passed cp_async_wait_all().
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
-                 : "memory");
-}
-
-// The same with the destination as a shared-window address (from smem_addr).
+// Per-thread 8-byte copy global -> shared, the destination given as a
+// shared-window address (from smem_addr); both addresses 8-byte aligned.
+// Complete for the issuing thread once it has passed cp_async_wait_all().
 __device__ __forceinline__ void cp_async8_s(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-// Makes barrier initialisation visible to the asynchronous proxy.
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Orders this thread's earlier generic-proxy shared-memory accesses before
-// later asynchronous-proxy ones (a bulk copy overwriting a buffer just read).
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One arrival that also announces `bytes` of transaction count.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// Global -> shared bulk copy completing on `bar`.  Both addresses 16-byte
-// aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
-                                              uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for phase `parity` of `bar` with an iteration limit; false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  uint32_t max_iter = 1u << 20) {
-    for (uint32_t i = 0; i < max_iter; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
 }
 
 }  // namespace mpr
