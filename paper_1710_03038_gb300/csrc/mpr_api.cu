@@ -47,7 +47,7 @@ constexpr double kPiD = 3.14159265358979323846;
 // Byte offsets of the workspace regions of one context.
 struct Layout {
     size_t img, ctl, ch_a, ch_cnt, ch_last, ch_ecur, ch_elast, ch_esum, ch_esum2;
-    size_t zst, gst, outst, eout, samp, slot_map, tiles, counts, halo, scratch;
+    size_t zst, gst, outst, eout, samp, slot_map, tiles, counts, halo, tile_list, scratch;
     size_t slot_pos, slot_ref, slot_cs, acc1, acc2, state, newton, hist, sub;
     size_t total;
     long long n_slots;   // slot space over all images
@@ -125,6 +125,7 @@ Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_im
     L.tiles = take(sizeof(TileDesc) * g.n_tiles);
     L.counts = take(sizeof(int) * 2 * g.n_tiles);
     L.halo = take(sizeof(int2) * (size_t)g.n_tiles * 2 * g.halo_cap);
+    L.tile_list = take(sizeof(int) * 2 * (size_t)g.n_tiles);
     L.scratch = take(sizeof(double) * 4 * g.n_img);
     L.n_slots = 0;
     L.n_state = 0;
@@ -177,6 +178,7 @@ struct mpr_ctx {
     int* d_slot_map = nullptr;
     TileDesc* d_tiles = nullptr;
     int2* d_halo = nullptr;
+    int* d_tile_list = nullptr;  // per colour: the tiles of the light launch, then the heavy ones
     uint32_t* d_slot_pos = nullptr;
     uint2* d_slot_ref = nullptr;
     float2* d_slot_cs = nullptr;
@@ -193,7 +195,11 @@ struct mpr_ctx {
     // host mirrors
     std::vector<ImgDev> h_img;
     std::vector<long long> slots;
-    int gt[2] = {1, 1};           // tiled: table entries for the pass of colour c
+    int gt[2] = {1, 1};           // tiled: table entries for the pass of colour c (largest tile)
+    // tiled: tiles whose table fits the shared memory of a full SM of blocks run
+    // in one launch (gt_light entries), the rest in a second one (gt entries)
+    int gt_light[2] = {1, 1};
+    int n_light[2] = {0, 0};
     uint32_t sweep = 0, equil_index = 0;
     long long n_meas_done = 0;
     bool T_set = false;
@@ -231,6 +237,7 @@ void bind_views(mpr_ctx* c) {
     c->d_slot_map = at<int>(w, L.slot_map);
     c->d_tiles = at<TileDesc>(w, L.tiles);
     c->d_halo = at<int2>(w, L.halo);
+    c->d_tile_list = at<int>(w, L.tile_list);
     c->d_slot_pos = at<uint32_t>(w, L.slot_pos);
     c->d_slot_ref = at<uint2>(w, L.slot_ref);
     c->d_slot_cs = at<float2>(w, L.slot_cs);
@@ -681,6 +688,50 @@ int pick_chain_group(const mpr_ctx* c) {
     return cg >= n ? n : cg;
 }
 
+// Sorts the tiles of each colour pass into a light launch, whose tables let
+// an SM hold as many blocks as its threads allow, and a heavy launch with the
+// rest (tiles inside large gap blocks, say), so that a few dense tiles do not
+// cut the occupancy of every block.  Without heavy tiles a pass is one launch.
+mpr_status split_tiles(mpr_ctx* c, const std::vector<TileDesc>& tiles, cudaStream_t s) {
+    const Geometry& g = c->g;
+    size_t fixed = 0, per = 0;
+    int blocks = 1, dev = 0, sm_bytes = 0, reserved = 0;
+    tiled_smem_shape(g.tx, g.ty, pick_chain_group(c), &fixed, &per, &blocks);
+    MPR_CUDA(cudaGetDevice(&dev));
+    MPR_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    MPR_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const size_t budget = (size_t)sm_bytes / (size_t)blocks - (size_t)reserved;
+    const int cap = budget > fixed + per ? (int)((budget - fixed) / per) : 1;
+    const int n = g.n_tiles;
+    std::vector<int> list(2 * (size_t)n);
+    bool split = false;
+    for (int col = 0; col < 2; ++col) {
+        int gmax = 1, glight = 1, nl = 0;
+        std::vector<int> heavy;
+        for (int t = 0; t < n; ++t) {
+            const int e = tiles[t].cnt[col ^ 1] + tiles[t].halo_cnt[col] + 1;
+            gmax = std::max(gmax, e);
+            if (e <= cap) {
+                list[(size_t)col * n + nl++] = t;
+                glight = std::max(glight, e);
+            } else {
+                heavy.push_back(t);
+            }
+        }
+        for (size_t k = 0; k < heavy.size(); ++k) list[(size_t)col * n + nl + k] = heavy[k];
+        c->gt[col] = gmax;
+        c->gt_light[col] = glight;
+        c->n_light[col] = nl;
+        split = split || nl < n;
+    }
+    if (split) {
+        MPR_CUDA(cudaMemcpyAsync(c->d_tile_list, list.data(), sizeof(int) * list.size(),
+                                 cudaMemcpyHostToDevice, s));
+        MPR_CUDA(cudaStreamSynchronize(s));
+    }
+    return MPR_OK;
+}
+
 mpr_status sub_workspace_size(const mpr_params& p, const mpr_T_opts& o, int n_img, const int* Lx,
                               const int* Ly, size_t* bytes);
 
@@ -895,12 +946,11 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
         MPR_CUDA(cudaMemsetAsync(c->d_slot_pos, 0xFF, sizeof(uint32_t) * c->L.n_slots, s));
         MPR_CUDA(launch_tile_fill(c->d_img, c->d_tiles, g.n_tiles, d_gap, tx, ty, c->d_slot_pos,
                                   c->d_slot_map, c->d_halo, g.halo_cap, s));
-        // table size of each pass from the ring lists just built
-        int* gt = at<int>(c->ws, c->L.counts);
-        MPR_CUDA(cudaMemsetAsync(gt, 0, sizeof(int) * 2, s));
-        MPR_CUDA(launch_tile_gt(c->d_tiles, g.n_tiles, gt, s));
-        MPR_CUDA(cudaMemcpyAsync(c->gt, gt, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        // table entries of every tile and pass from the ring lists just built
+        MPR_CUDA(cudaMemcpyAsync(tiles.data(), c->d_tiles, sizeof(TileDesc) * g.n_tiles,
+                                 cudaMemcpyDeviceToHost, s));
         MPR_CUDA(cudaStreamSynchronize(s));
+        MPR_TRY(split_tiles(c, tiles, s));
     }
     long long maxn = 0;
     for (int i = 0; i < n_img; ++i) maxn = std::max(maxn, (long long)Lx[i] * Ly[i]);
@@ -1000,10 +1050,24 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
     for (int k = 0; k < n; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
             a.colour = colour;
-            a.gt = c->gt[colour];
             a.flags = base | ((record && colour == 1) ? kEnergy : 0);
-            cudaError_t e = tiled ? launch_tiled_pass(a, c->g.n_tiles, c->g.tx, c->g.ty, s)
-                                  : launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
+            cudaError_t e = cudaSuccess;
+            if (!tiled) {
+                e = launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
+            } else {
+                const int nt = c->g.n_tiles, nl = c->n_light[colour];
+                a.tile_list = nl < nt ? c->d_tile_list + (size_t)colour * nt : nullptr;
+                if (nl > 0) {  // the light tiles (all of them without a heavy launch)
+                    a.tile_base = 0;
+                    a.gt = nl < nt ? c->gt_light[colour] : c->gt[colour];
+                    e = launch_tiled_pass(a, nl, c->g.tx, c->g.ty, s);
+                }
+                if (e == cudaSuccess && nl < nt) {
+                    a.tile_base = nl;
+                    a.gt = c->gt[colour];
+                    e = launch_tiled_pass(a, nt - nl, c->g.tx, c->g.ty, s);
+                }
+            }
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
         }
         end_sweep_kernel<<<1, 1024, 0, s>>>(c->d_img, c->ch, c->d_ctl, c->g.n_img, c->g.n_chains,

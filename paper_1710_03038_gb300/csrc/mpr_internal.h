@@ -93,6 +93,8 @@ struct SweepArgs {
     int flags;
     int halo_cap;
     int gt;                    // tiled: table entries per chain pair for this pass
+    const int* tile_list;      // tiled: tile of block b is tile_list[tile_base + b] (null: b)
+    int tile_base;
     int n_img;
     uint32_t img_tag;          // OR-ed into the image field of the counter (1 << 30: T lattices)
 };
@@ -121,8 +123,10 @@ cudaError_t launch_tile_const(const ImgDev* img, const TileDesc* tiles, int n_ti
                               int tile_y, const uint32_t* slot_pos, const int2* halo, int halo_cap,
                               const float* samp, float q, uint2* slot_ref, float2* slot_cs,
                               cudaStream_t s);
-// out[c] = table entries of the pass of colour c (out must hold zeros)
-cudaError_t launch_tile_gt(const TileDesc* tiles, int n_tiles, int* out, cudaStream_t s);
+// Shared memory of a colour-pass block: fixed part plus `per_entry` bytes per
+// table entry; `blocks` = the most blocks an SM can hold by their threads.
+void tiled_smem_shape(int tile_x, int tile_y, int chain_group, size_t* fixed, size_t* per_entry,
+                      int* blocks);
 
 // float offset of gap slot k (tiled) or site k (plain) of a realisation
 __host__ __device__ inline long long state_index(const ImgDev& I, int chain, long long k) {

@@ -3,6 +3,7 @@
 // one translation unit per tile shape).
 #include "mpr_device.cuh"
 #include "mpr_internal.h"
+#include "mpr_tiled_kernel.cuh"
 
 namespace mpr {
 
@@ -171,25 +172,23 @@ __global__ void tile_const_kernel(const ImgDev* img, const TileDesc* tiles, int 
     }
 }
 
-// Table entries the pass of colour c needs for its largest tile: the tile's
-// other-colour gap cells, its ring cells, and the zero entry (out[c], atomic
-// maxima; out must hold zeros).
-__global__ void tile_gt_kernel(const TileDesc* tiles, int n_tiles, int* out) {
-    int m0 = 0, m1 = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
-        const TileDesc& T = tiles[t];
-        m0 = max(m0, T.cnt[1] + T.halo_cnt[0] + 1);
-        m1 = max(m1, T.cnt[0] + T.halo_cnt[1] + 1);
-    }
-    m0 = __reduce_max_sync(0xffffffffu, m0);
-    m1 = __reduce_max_sync(0xffffffffu, m1);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(out, m0);
-        atomicMax(out + 1, m1);
+}  // namespace
+
+void tiled_smem_shape(int tx, int ty, int chain_group, size_t* fixed, size_t* per_entry,
+                      int* blocks) {
+    const int P = tiled::pairs_for_group(chain_group);
+    *per_entry = sizeof(float4) * P;
+    if (tx == 32 && ty == 16) {
+        *fixed = tiled::Cfg<32, 16, 8>::off_tab;
+        *blocks = 1024 / tiled::Cfg<32, 16, 8>::NT;
+    } else if (tx == 32 && ty == 32) {
+        *fixed = tiled::Cfg<32, 32, 8>::off_tab;
+        *blocks = 1024 / tiled::Cfg<32, 32, 8>::NT;
+    } else {
+        *fixed = tiled::Cfg<16, 16, 4>::off_tab;
+        *blocks = 1024 / tiled::Cfg<16, 16, 4>::NT;
     }
 }
-
-}  // namespace
 
 bool tiled_config_supported(int tx, int ty) {
     return (tx == 32 && ty == 16) || (tx == 16 && ty == 16) || (tx == 32 && ty == 32);
@@ -235,10 +234,5 @@ cudaError_t launch_tile_const(const ImgDev* img, const TileDesc* tiles, int n_ti
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_gt(const TileDesc* tiles, int n_tiles, int* out, cudaStream_t s) {
-    const int blocks = std::min(152, (n_tiles + 255) / 256);
-    tile_gt_kernel<<<std::max(blocks, 1), 256, 0, s>>>(tiles, n_tiles, out);
-    return cudaGetLastError();
-}
 
 }  // namespace mpr

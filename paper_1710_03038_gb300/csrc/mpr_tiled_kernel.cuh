@@ -78,7 +78,8 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const int warp = tid >> 5;
     const int p = lane & (P - 1);  // pair of the group (fixed per thread: NT is a multiple of P)
     const int s = lane / P;        // site within a warp step
-    const TileDesc* Tp = a.tiles + blockIdx.x;
+    const int tile = a.tile_list ? a.tile_list[a.tile_base + blockIdx.x] : (int)blockIdx.x;
+    const TileDesc* Tp = a.tiles + tile;
     const int c = a.colour;
     const int oc = c ^ 1;
     const int n_own = Tp->cnt[c];
@@ -104,7 +105,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const long long cp = I.sstride;  // floats from one slot to the next
     // this lane's pair at slot 0 (8-byte aligned: state_off, cp, r0 are even)
     float* st = a.state + I.state_off + r0 + 2 * p;
-    const int spread = blockIdx.x & (kSpread - 1);
+    const int spread = tile & (kSpread - 1);
 
     // -- table of the other colour, raw: entry 1 + e, pair p ----------------------
     // Each thread copies the angle pairs of its entries e = tid / P (mod NT / P)
@@ -144,7 +145,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     if (has0) {
         const int k_first = (max(n_oth - e_lo, 0) + NTP - 1) / NTP;  // steps to the ring
         const int e_first = e_lo + k_first * NTP;
-        const int2* h = a.halo + ((long long)blockIdx.x * 2 + c) * a.halo_cap + (e_first - n_oth);
+        const int2* h = a.halo + ((long long)tile * 2 + c) * a.halo_cap + (e_first - n_oth);
         uint32_t dst = smem_addr(tab_lo) + (uint32_t)k_first * kDstStep;
         for (int e = e_first; e < n_ent; e += NTP, h += NTP, dst += kDstStep)
             cp_async8_s(dst, st + (long long)h->x * cp);

@@ -227,6 +227,52 @@ def test_tile_shapes_and_chain_groups_agree_bitwise(tile):
             assert np.array_equal(a, b)
 
 
+def _largest_table(gap, tx=16, ty=16):
+    """Largest other-colour table of a colour pass over the tiles of one image: the
+    gap cells of the other colour inside the tile and in its 1-cell ring (corners
+    excluded), plus the zero entry."""
+    Ly, Lx = gap.shape
+    best = 0
+    for y0 in range(0, Ly, ty):
+        for x0 in range(0, Lx, tx):
+            for c in (0, 1):
+                n = 0
+                for y in range(max(y0 - 1, 0), min(y0 + ty + 1, Ly)):
+                    for x in range(max(x0 - 1, 0), min(x0 + tx + 1, Lx)):
+                        corner = not (y0 <= y < y0 + ty) and not (x0 <= x < x0 + tx)
+                        if not corner and (x + y) % 2 != c and gap[y, x]:
+                            n += 1
+                best = max(best, n + 1)
+    return best
+
+
+def test_heavy_tiles_launch_separately_and_agree_bitwise():
+    """32 chains in one group: a tile inside the block gap needs a table too large for a
+    full SM of blocks and runs in the pass's second (heavy) launch; states, energies
+    and sums still equal the plain path's."""
+    zs, gs = ragged_images()
+    gs[0][16:32, 32:48] = 1  # one 16x16 tile entirely gap
+    # 16 pairs x 16 B per entry: more than 92 entries leaves fewer than 8 blocks per SM
+    assert _largest_table(gs[0]) > 92
+    R = 32
+    out = []
+    for path, kw in (("plain", {}), ("tiled", {"chain_group": 32})):
+        ctx = make_ctx(zs, gs, R, path, **kw)
+        ctx.set_T([0.2, 0.2, 0.1, 0.4])
+        ctx.sweep(3, "equil", record_energy=True)
+        info = ctx.chain_info()
+        ctx.sweep(2, "measure")
+        out.append(([s.cpu().numpy() for s in ctx.get_state()], info,
+                    [p.cpu().numpy() for p in ctx.predict()]))
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1]["a"], out[1][1]["a"])
+    assert np.array_equal(out[0][1]["accepted"], out[1][1]["accepted"])
+    assert np.allclose(out[0][1]["e_last"], out[1][1]["e_last"], rtol=0, atol=1e-6)
+    for a, b in zip(out[0][2], out[1][2]):
+        assert np.allclose(a, b, rtol=1e-6, atol=1e-5)
+
+
 def test_determinism_same_state_same_result():
     """Colour-race canary: the same sweep from the same state gives identical bits."""
     zs, gs = ragged_images()
