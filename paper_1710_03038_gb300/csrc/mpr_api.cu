@@ -688,6 +688,26 @@ int pick_chain_group(const mpr_ctx* c) {
     return cg >= n ? n : cg;
 }
 
+// Chain ranges of a tiled pass: whole groups of the automatic (or requested)
+// size, then, when the chain count is not a multiple of it, the remaining
+// chains as one smaller group in a launch of their own, so that they do not
+// occupy a full group's lanes (100 chains: 3 x 32, then 4).
+struct ChainRange {
+    int chain0, chain_end, group;
+};
+
+int chain_ranges(const mpr_ctx* c, ChainRange out[2]) {
+    const int n = c->g.n_chains, cg = pick_chain_group(c);
+    const int rem = cg < n ? n % cg : 0;
+    if (rem == 0) {
+        out[0] = {0, n, cg};
+        return 1;
+    }
+    out[0] = {0, n - rem, cg};
+    out[1] = {n - rem, n, rem};
+    return 2;
+}
+
 // Sorts the tiles of each colour pass into a light launch, whose tables let
 // an SM hold as many blocks as its threads allow, and a heavy launch with the
 // rest (tiles inside large gap blocks, say), so that a few dense tiles do not
@@ -1038,6 +1058,10 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
     a.J = (float)c->p.J;
     a.n_chains = c->g.n_chains;
     a.chain_group = pick_chain_group(c);
+    a.chain0 = 0;
+    a.chain_end = c->g.n_chains;
+    ChainRange cr[2];
+    const int n_cr = chain_ranges(c, cr);
     a.halo_cap = c->g.halo_cap;
     a.n_img = c->g.n_img;
     a.img_tag = c->img_tag;
@@ -1056,6 +1080,10 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
                 e = launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
             } else {
                 const int nt = c->g.n_tiles, nl = c->n_light[colour];
+                // whole chain groups: light tiles, then heavy ones
+                a.chain0 = cr[0].chain0;
+                a.chain_end = cr[0].chain_end;
+                a.chain_group = cr[0].group;
                 a.tile_list = nl < nt ? c->d_tile_list + (size_t)colour * nt : nullptr;
                 if (nl > 0) {  // the light tiles (all of them without a heavy launch)
                     a.tile_base = 0;
@@ -1066,6 +1094,15 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
                     a.tile_base = nl;
                     a.gt = c->gt[colour];
                     e = launch_tiled_pass(a, nt - nl, c->g.tx, c->g.ty, s);
+                }
+                if (e == cudaSuccess && n_cr > 1) {  // the remaining chains, every tile
+                    a.chain0 = cr[1].chain0;
+                    a.chain_end = cr[1].chain_end;
+                    a.chain_group = cr[1].group;
+                    a.tile_list = nullptr;
+                    a.tile_base = 0;
+                    a.gt = c->gt[colour];
+                    e = launch_tiled_pass(a, nt, c->g.tx, c->g.ty, s);
                 }
             }
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
@@ -1103,8 +1140,14 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
             if (c->g.path == MPR_PATH_TILED) {
                 SweepArgs a{};
                 a.n_chains = c->g.n_chains;
-                a.chain_group = pick_chain_group(c);
-                MPR_CUDA(launch_tiled_pass(a, 0, c->g.tx, c->g.ty, s, true));
+                ChainRange cr[2];
+                const int n_cr = chain_ranges(c, cr);
+                for (int r = 0; r < n_cr; ++r) {
+                    a.chain0 = cr[r].chain0;
+                    a.chain_end = cr[r].chain_end;
+                    a.chain_group = cr[r].group;
+                    MPR_CUDA(launch_tiled_pass(a, 0, c->g.tx, c->g.ty, s, true));
+                }
             }
             MPR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             const mpr_status st = launch_sweeps(c, n, phase, flags, stats, accumulate, s);

@@ -89,6 +89,7 @@ struct SweepArgs {
     float q, inv_q, two_pi_q, J;
     int n_chains;
     int chain_group;
+    int chain0, chain_end;     // tiled: the launch covers chains [chain0, chain_end), chain0 even
     int colour;
     int flags;
     int halo_cap;

@@ -196,8 +196,9 @@ bool tiled_config_supported(int tx, int ty) {
 
 cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, cudaStream_t s,
                               bool setup_only) {
-    if (a.chain_group < 1 || (a.chain_group % 2 != 0 && a.chain_group < a.n_chains) ||
-        a.chain_group > 32)
+    if (a.chain_group < 1 || a.chain_group > 32 || (a.chain0 & 1) || a.chain0 < 0 ||
+        a.chain_end <= a.chain0 || a.chain_end > a.n_chains ||
+        (a.chain_group % 2 != 0 && a.chain_group < a.chain_end - a.chain0))
         return cudaErrorInvalidValue;
     if (tx == 32 && ty == 16) return launch_tiled_32x16(a, n_tiles, s, setup_only);
     if (tx == 16 && ty == 16) return launch_tiled_16x16(a, n_tiles, s, setup_only);

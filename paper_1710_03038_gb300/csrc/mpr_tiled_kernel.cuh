@@ -92,8 +92,8 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const int n_oth = Tp->cnt[oc];
     const int n_halo = Tp->halo_cnt[c];
     const ImgDev& I = a.img[t_img];
-    const int r0 = blockIdx.y * a.chain_group;
-    const int ng = min(a.chain_group, a.n_chains - r0);
+    const int r0 = a.chain0 + blockIdx.y * a.chain_group;
+    const int ng = min(a.chain_group, a.chain_end - r0);
     const bool has0 = 2 * p < ng;      // this lane's pair exists
     const bool has1 = 2 * p + 1 < ng;  // and has a second chain
     const bool accum2 = ACC && (a.flags & kAccumulate2) != 0;
@@ -307,7 +307,7 @@ cudaError_t launch_one(const SweepArgs& a, int n_tiles, cudaStream_t s, bool set
     }
     if (setup_only) return cudaSuccess;
     if (a.gt < 1 || a.gt > C::GT) return cudaErrorInvalidValue;
-    dim3 grid(n_tiles, (a.n_chains + a.chain_group - 1) / a.chain_group);
+    dim3 grid(n_tiles, (a.chain_end - a.chain0 + a.chain_group - 1) / a.chain_group);
     tiled_pass_kernel<TX, TY, NW, P, ACC><<<grid, C::NT, C::smem_for(a.gt, P), s>>>(a);
     return cudaGetLastError();
 }
