@@ -411,6 +411,46 @@ def run_reference(args):
     return line
 
 
+def workload_rates(names):
+    """Sweep rates of the named synthetic workloads (tiled path, default launch
+    configuration, temperature from the estimate): one JSON line per workload with
+    the gap site-updates/s of 20 equilibration and of 20 measurement sweeps (graph
+    replays, CUDA events) and the HBM fraction at 4 (1/f + 1) bytes per update.
+    These are the parity workloads' rates, not benchmark lines."""
+    import torch
+    import synthetic
+    import paper_1710_03038_gb300 as mpr
+    peak, peak_kind = _peaks()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    for name in names:
+        w = synthetic.workload(name)
+        zs = [torch.from_numpy(z).cuda() for z in w.z]
+        gs = [torch.from_numpy(g).cuda() for g in w.gap]
+        P = int(sum(int(g.sum()) for g in w.gap))
+        N = int(sum(g.size for g in w.gap))
+        f = P / N
+        ctx = mpr.Context(zs, gs, chains=w.chains, params=mpr.Params(seed=3), device="cuda")
+        ctx.estimate_T_async()
+        ctx.sweep(10, "equil")
+        torch.cuda.synchronize()
+        out = {"workload": w.name, "images": len(w.z), "sites": N, "gap_fraction": round(f, 4),
+               "realisations": w.chains, "unit": UNIT, "peak_gbs": peak, "peak_kind": peak_kind}
+        for phase in ("equil", "measure"):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.sweep(20, phase)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 20
+            rate = P * w.chains / (ms / 1e3)
+            out[phase] = {"ms_per_sweep": round(ms, 4), "value": float(f"{rate:.4g}"),
+                          "hbm_frac": round(rate * 4.0 * (1.0 / f + 1.0) / (peak * 1e9), 4)}
+        ctx.close()
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,8 +466,14 @@ def main():
                     help="image side (4096 is the benchmark; smaller sides are for profiler captures)")
     ap.add_argument("--T", type=float, default=None,
                     help="fixed temperature instead of the estimate (profiler captures)")
+    ap.add_argument("--rates", nargs="*", default=None, metavar="WORKLOAD",
+                    help="print the sweep rates of these synthetic workloads (all when none "
+                         "is named) instead of the benchmark line")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.rates is not None:
+        import synthetic
+        workload_rates(args.rates or [n for n in synthetic.WORKLOADS if n != "grf64"])
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
