@@ -78,7 +78,8 @@ typedef struct {
     int freeze_a_in_measure; /* 1: keep the last equilibration a while sampling; 0: a = 1
                                 as printed in Alg. 2 step 5.2                                   */
     int path;                /* mpr_path                                                       */
-    int tile_x, tile_y;      /* tiled path tile shape; 0 = autotuned                          */
+    int tile_x, tile_y;      /* tiled path tile shape (16x16, 32x16 or 32x32); 0 = 16x16
+                                (mpr_autotune times all three)                                 */
     int chain_group;         /* tiled path: chains per thread block, even or >= n_chains;
                                 values above 32 act as 32; 0 = automatic                       */
     int literal_or;          /* 1: over-relaxation as printed in Eq. over-relax (q = 1 field,

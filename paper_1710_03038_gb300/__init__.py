@@ -39,7 +39,7 @@ class Params:
     seed: int = 0x2545F4914F6CDD1D
     freeze_a_in_measure: bool = True
     path: str = "tiled"          # "tiled" (batched) or "plain"
-    tile: tuple = (0, 0)         # (tile_x, tile_y); (0, 0) = automatic
+    tile: tuple = (0, 0)         # (tile_x, tile_y); (0, 0) = 16x16
     chain_group: int = 0         # chains per thread block; 0 = automatic
     literal_or: bool = False     # printed q = 1 over-relaxation (plain path, comparison only)
     use_graphs: bool = True      # replay captured CUDA graphs of sweep runs (non-default streams)
