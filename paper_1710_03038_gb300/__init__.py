@@ -147,7 +147,9 @@ class Context:
             zf = zs[0].reshape(-1)
             gf = gs[0].reshape(-1).view(torch.uint8)
             where = _lib.MPR_HOST
-            ng = [int(np.count_nonzero(gf.numpy()))]
+            # no host pass over the mask: the workspace is sized for the worst case
+            # (every site a gap) and the library counts the gaps on the device
+            ng = None
         else:
             zn = [np.asarray(t.cpu() if isinstance(t, torch.Tensor) else t, dtype=np.float32) for t in zs]
             gn = [(np.asarray(t.cpu() if isinstance(t, torch.Tensor) else t) != 0).astype(np.uint8) for t in gs]
@@ -160,7 +162,8 @@ class Context:
         Lx = int_array([s[1] for s in self.shapes])
         cp, co = self.params.c(), self.topts.c()
         nbytes = C.c_size_t()
-        call("mpr_workspace_size", self.n_img, Lx, Ly, i64_array(ng), self.chains, C.byref(cp),
+        call("mpr_workspace_size", self.n_img, Lx, Ly, i64_array(ng) if ng is not None else None,
+             self.chains, C.byref(cp),
              C.byref(co), C.byref(nbytes))
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
         self._ctx = C.c_void_p()
