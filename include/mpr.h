@@ -127,7 +127,8 @@ mpr_status mpr_workspace_size(int n_img, const int* Lx, const int* Ly, const int
  * angles with Eq. map (extremes over sample sites), builds the gap layout,
  * draws the hot start of every realisation (gap angles ~ U(0, 2 pi), step
  * 1.8), sets a = 1, and computes the sample specific energy e_s of
- * Eq. mpr-sse (mean over unordered sample-sample bonds, FP64).
+ * Eq. mpr-sse (mean over unordered sample-sample bonds; FP32 bond terms
+ * summed in FP64).
  *  z       [sum Lx*Ly] float values; entries at gap pixels are ignored
  *  gap     [sum Lx*Ly] uint8, nonzero = missing
  *  where   whether z and gap are host or device pointers

@@ -296,8 +296,10 @@ __global__ void map_kernel(const ImgDev* img, const float* z, const uint8_t* gap
 
 // Sample specific energy (Eq. mpr-sse) sums: -J sum cos(q dphi) over sample
 // pairs (right and down bonds), FP64.
-__device__ __forceinline__ double bond_energy(double d, double q, double J, int gmrf) {
-    return gmrf ? J * (d * d / (2.0 * kPiD * kPiD) - 1.0) : -J * cos(q * d);
+// One bond's energy in FP32 (summed in FP64 by the caller); the same
+// expression as the allocation-free entry point's.
+__device__ __forceinline__ float bond_energy(float d, float q, float J, int gmrf) {
+    return gmrf ? J * (d * d * (float)(0.5 / (kPiD * kPiD)) - 1.0f) : -J * cosf(q * d);
 }
 
 __global__ void sample_energy_kernel(const ImgDev* img, const float* samp, double q, double J,
@@ -313,11 +315,11 @@ __global__ void sample_energy_kernel(const ImgDev* img, const float* samp, doubl
         const int x = (int)(i % I.Lx), y = (int)(i / I.Lx);
         if (x + 1 < I.Lx) {
             const float w = samp[I.site_off + i + 1];
-            if (w >= 0.0f) { s += bond_energy((double)v - (double)w, q, J, gmrf); ++cnt; }
+            if (w >= 0.0f) { s += (double)bond_energy(v - w, (float)q, (float)J, gmrf); ++cnt; }
         }
         if (y + 1 < I.Ly) {
             const float w = samp[I.site_off + i + I.Lx];
-            if (w >= 0.0f) { s += bond_energy((double)v - (double)w, q, J, gmrf); ++cnt; }
+            if (w >= 0.0f) { s += (double)bond_energy(v - w, (float)q, (float)J, gmrf); ++cnt; }
         }
     }
     s = warp_sum(s);

@@ -117,7 +117,7 @@ __global__ void noalloc_extremes_final_kernel(const Partial* part, ImgStat* stat
 
 // Phase 3: sample-sample bond sums with the angles of Eq. map computed on the
 // fly exactly as the context's initialisation computes them (FP64 map,
-// rounded to FP32 once; FP64 cosines of the FP32 angle differences).
+// rounded to FP32 once; FP32 bond terms -J cos(q (v - w)) summed in FP64).
 __global__ void noalloc_pairs_kernel(const __grid_constant__ Shapes S, const float* z,
                                      const uint8_t* gap, const ImgStat* stat, double q, double J,
                                      Partial* part) {
@@ -140,12 +140,12 @@ __global__ void noalloc_pairs_kernel(const __grid_constant__ Shapes S, const flo
         const float v = (float)(((double)zi[i] - zmin) * scale);
         if (x + 1 < Lx && !gi[i + 1]) {
             const float w = (float)(((double)zi[i + 1] - zmin) * scale);
-            s -= J * cos(q * ((double)v - (double)w));
+            s -= (double)((float)J * cosf((float)q * (v - w)));
             ++cnt;
         }
         if (y + 1 < Ly && !gi[i + Lx]) {
             const float w = (float)(((double)zi[i + Lx] - zmin) * scale);
-            s -= J * cos(q * ((double)v - (double)w));
+            s -= (double)((float)J * cosf((float)q * (v - w)));
             ++cnt;
         }
     }
