@@ -135,7 +135,7 @@ Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_im
     }
     L.slot_pos = take(tiled ? sizeof(uint32_t) * L.n_slots : 0);
     L.slot_ref = take(tiled ? sizeof(uint2) * L.n_slots : 0);
-    L.slot_cs = take(tiled ? sizeof(float2) * L.n_slots : 0);
+    L.slot_cs = take(tiled ? sizeof(float4) * L.n_slots : 0);
     L.acc1 = take(sizeof(double) * L.n_slots);
     L.acc2 = take(sizeof(double) * L.n_slots);
     L.state = take(sizeof(float) * L.n_state);
@@ -181,7 +181,7 @@ struct mpr_ctx {
     int* d_tile_list = nullptr;  // per colour: the tiles of the light launch, then the heavy ones
     uint32_t* d_slot_pos = nullptr;
     uint2* d_slot_ref = nullptr;
-    float2* d_slot_cs = nullptr;
+    float4* d_slot_cs = nullptr;
     double* d_acc1 = nullptr;
     double* d_acc2 = nullptr;
     float* d_state = nullptr;
@@ -240,7 +240,7 @@ void bind_views(mpr_ctx* c) {
     c->d_tile_list = at<int>(w, L.tile_list);
     c->d_slot_pos = at<uint32_t>(w, L.slot_pos);
     c->d_slot_ref = at<uint2>(w, L.slot_ref);
-    c->d_slot_cs = at<float2>(w, L.slot_cs);
+    c->d_slot_cs = at<float4>(w, L.slot_cs);
     c->d_acc1 = at<double>(w, L.acc1);
     c->d_acc2 = at<double>(w, L.acc2);
     c->d_state = at<float>(w, L.state);
@@ -652,10 +652,12 @@ mpr_status check_params(const mpr_params* p) {
     if (p->chain_group < 0) return fail(MPR_ERR_INVALID_ARG, "chain_group < 0");
     if (p->model != MPR_MODEL_MPR && p->model != MPR_MODEL_GMRF)
         return fail(MPR_ERR_INVALID_ARG, "unknown model");
-    if (p->model == MPR_MODEL_GMRF && p->path != MPR_PATH_PLAIN)
-        return fail(MPR_ERR_INVALID_ARG, "the GMRF variant runs on the plain path");
-    if (p->literal_or && p->path != MPR_PATH_PLAIN)
-        return fail(MPR_ERR_INVALID_ARG, "the printed (q = 1) over-relaxation runs on the plain path");
+    if (p->model == MPR_MODEL_GMRF && p->literal_or)
+        return fail(MPR_ERR_INVALID_ARG, "the printed over-relaxation belongs to the MPR model");
+    if (p->path == MPR_PATH_TILED && (p->model == MPR_MODEL_GMRF || p->literal_or) &&
+        !((p->tile_x == 0 && p->tile_y == 0) || (p->tile_x == 16 && p->tile_y == 16)))
+        return fail(MPR_ERR_INVALID_ARG,
+                    "the GMRF model and the printed over-relaxation run with 16 x 16 tiles");
     return MPR_OK;
 }
 
@@ -672,6 +674,11 @@ void pick_tiles(const mpr_params& p, int n_img, const int* Lx, const int* Ly, in
     // of the three shapes on 4096^2 images at 40 % gaps)
     tx = 16;
     ty = 16;
+}
+
+// Model bits of the sweep flags (SweepFlags) for a parameter set.
+int model_flags(const mpr_params& p) {
+    return (p.literal_or ? kLiteralOR : 0) | (p.model == MPR_MODEL_GMRF ? kGMRF : 0);
 }
 
 // Chains per thread block of the tiled pass (even, or covering every chain;
@@ -718,7 +725,7 @@ mpr_status split_tiles(mpr_ctx* c, const std::vector<TileDesc>& tiles, cudaStrea
     const Geometry& g = c->g;
     size_t fixed = 0, per = 0;
     int blocks = 1, dev = 0, sm_bytes = 0, reserved = 0;
-    tiled_smem_shape(g.tx, g.ty, pick_chain_group(c), &fixed, &per, &blocks);
+    tiled_smem_shape(g.tx, g.ty, pick_chain_group(c), model_flags(c->p), &fixed, &per, &blocks);
     MPR_CUDA(cudaGetDevice(&dev));
     MPR_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     MPR_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
@@ -781,7 +788,7 @@ mpr_status sub_workspace_size(const mpr_params& p, const mpr_T_opts& o, int n_im
     for (int i = 0; i < n_img; ++i) L[i] = default_T_side(Lx[i], Ly[i], o);
     mpr_params sp = p;
     sp.literal_or = 0;
-    sp.path = p.model == MPR_MODEL_GMRF ? MPR_PATH_PLAIN : MPR_PATH_TILED;
+    sp.path = MPR_PATH_TILED;
     sp.tile_x = sp.tile_y = 0;
     sp.chain_group = 0;
     return workspace_size_impl(n_img, L.data(), L.data(), nullptr, o.chains, sp, o, false, false,
@@ -981,7 +988,8 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
     MPR_CUDA(cudaGetLastError());
     if (tiled)
         MPR_CUDA(launch_tile_const(c->d_img, c->d_tiles, g.n_tiles, tx, ty, c->d_slot_pos,
-                                   c->d_halo, g.halo_cap, c->d_samp, (float)c->p.q, c->d_slot_ref,
+                                   c->d_halo, g.halo_cap, c->d_samp, (float)c->p.q,
+                                   c->p.model == MPR_MODEL_GMRF ? 1 : 0, c->d_slot_ref,
                                    c->d_slot_cs, s));
     const uint2 key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
     for (int i = 0; i < n_img; ++i) {
@@ -1070,8 +1078,7 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
     int base = 0;
     if (!equil && accumulate) base |= kAccumulate | kAccumulate2;
     if (!equil && !c->p.freeze_a_in_measure) base |= kAlphaOne;
-    if (c->p.literal_or) base |= kLiteralOR;
-    if (c->p.model == MPR_MODEL_GMRF) base |= kGMRF;
+    base |= model_flags(c->p);
     const bool tiled = c->g.path == MPR_PATH_TILED;
     for (int k = 0; k < n; ++k) {
         for (int colour = 0; colour < 2; ++colour) {
@@ -1142,6 +1149,7 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
             if (c->g.path == MPR_PATH_TILED) {
                 SweepArgs a{};
                 a.n_chains = c->g.n_chains;
+                a.flags = model_flags(c->p);
                 ChainRange cr[2];
                 const int n_cr = chain_ranges(c, cr);
                 for (int r = 0; r < n_cr; ++r) {
@@ -1283,7 +1291,7 @@ mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly,
     if (!c->sub) { delete c; return fail(MPR_ERR_INVALID_ARG, "out of host memory"); }
     c->sub->p = c->p;
     c->sub->p.literal_or = 0;
-    c->sub->p.path = c->p.model == MPR_MODEL_GMRF ? MPR_PATH_PLAIN : MPR_PATH_TILED;
+    c->sub->p.path = MPR_PATH_TILED;
     c->sub->p.tile_x = c->sub->p.tile_y = 0;
     c->sub->p.chain_group = 0;
     c->sub->topt = c->topt;
@@ -1401,6 +1409,7 @@ mpr_status mpr_autotune(int n_img, const int* Lx, const int* Ly, int n_chains, m
             if (slot) *slot = -1.0;
             int cg = groups[gi];
             if (cg > 0 && cg >= n_chains) continue;  // same as covering every chain
+            if (!tiled_model_supported(tiles[ti][0], tiles[ti][1], model_flags(*p))) continue;
             mpr_ctx c;
             c.p = *p;
             c.p.tile_x = tiles[ti][0];

@@ -68,42 +68,88 @@ __device__ __forceinline__ void site_uniform_words(int x, int y, int colour, uin
 }
 
 // ---------------------------------------------------------- small math
-// sin(t) for |t| <= pi/2 from its Taylor series through t^13 (relative error
-// below one ulp on that interval); used for the half proposal step where the
-// hardware sine's absolute error would dominate.
-__device__ __forceinline__ float sin_taylor(float t) {
-    const float t2 = t * t;
-    float p = -1.0f / 6227020800.0f;          // -1/13!
-    p = fmaf(p, t2, 1.0f / 39916800.0f);       //  1/11!
-    p = fmaf(p, t2, -1.0f / 362880.0f);        // -1/9!
-    p = fmaf(p, t2, 1.0f / 5040.0f);           //  1/7!  (sign pattern of sin)
-    p = fmaf(p, t2, -1.0f / 120.0f);
-    p = fmaf(p, t2, 1.0f / 6.0f);
-    // sin t = t - t^3/3! + t^5/5! - ...  = t * (1 - t2 * (1/3! - t2 * (1/5! - ...)))
-    return t * fmaf(-t2, p, 1.0f);
+// Every realisation pair (2m, 2m + 1) is updated by one thread: both updates
+// run the same instruction sequence on different data, so the FP32 adds,
+// multiplies and FMAs of the pair are issued as packed FP32x2 instructions
+// (sm_100 and later), one issue slot for both realisations.  Each component
+// is rounded exactly as the scalar operation would be.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// c - a (one rounding, as the scalar subtraction)
+__device__ __forceinline__ float2 rsub2(float2 a, float2 c) { return __ffma2_rn(a, f2(-1.0f), c); }
+__device__ __forceinline__ float2 floor2(float2 a) { return make_float2(floorf(a.x), floorf(a.y)); }
+__device__ __forceinline__ float2 sel2(bool p0, bool p1, float2 a, float2 b) {
+    return make_float2(p0 ? a.x : b.x, p1 ? a.y : b.y);
 }
 
-// atan2(y, x) for |x| + |y| > 0: octant reduction to t = min/max in [0, 1]
-// and an odd degree-15 polynomial t P(t^2) for atan(t) whose coefficients
-// were fitted here (minimax in the absolute error on [0, 1], 3.8e-8 in exact
-// arithmetic; about 1.2e-7 rad in FP32 including the approximate reciprocal).
-__device__ __forceinline__ float atan2_poly(float y, float x) {
-    const float ax = fabsf(x), ay = fabsf(y);
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float t = __fdividef(mn, mx);
-    const float t2 = t * t;
-    float p = -0.004054575f;
-    p = fmaf(p, t2, 0.021862987f);
-    p = fmaf(p, t2, -0.05591237f);
-    p = fmaf(p, t2, 0.09642201f);
-    p = fmaf(p, t2, -0.1390863f);
-    p = fmaf(p, t2, 0.19946566f);
-    p = fmaf(p, t2, -0.3332986f);
-    p = fmaf(p, t2, 0.99999934f);
-    float r = p * t;
-    if (ay > ax) r = 1.57079632679489662f - r;
-    if (x < 0.0f) r = kPi - r;
-    return copysignf(r, y);
+// The hardware approximations, named explicitly.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+    float r;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float r;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// sin(t) for |t| <= 3 pi / 4 from its Taylor series through t^13 (relative
+// error below 3e-7 there, one ulp near 0); used for the half proposal step,
+// where the hardware sine's absolute error would dominate small steps.
+__device__ __forceinline__ float2 sin_taylor2(float2 t) {
+    const float2 t2 = mul2(t, t);
+    float2 p = f2(-1.0f / 6227020800.0f);          // -1/13!
+    p = fma2(p, t2, f2(1.0f / 39916800.0f));       //  1/11!
+    p = fma2(p, t2, f2(-1.0f / 362880.0f));        // -1/9!
+    p = fma2(p, t2, f2(1.0f / 5040.0f));           //  1/7!
+    p = fma2(p, t2, f2(-1.0f / 120.0f));
+    p = fma2(p, t2, f2(1.0f / 6.0f));
+    // sin t = t (1 - t^2 (1/3! - t^2 (1/5! - ...)))
+    return mul2(t, fma2(mul2(t2, f2(-1.0f)), p, f2(1.0f)));
+}
+
+// atan2(y, x) of both components for |x| + |y| > 0: octant reduction to
+// t = min/max in [0, 1] and an odd degree-15 polynomial t P(t^2) for atan(t)
+// whose coefficients were fitted here (minimax in the absolute error on
+// [0, 1], 3.8e-8 in exact arithmetic; about 1.2e-7 rad in FP32 including the
+// approximate reciprocal).
+__device__ __forceinline__ float2 atan2_pair(float2 y, float2 x) {
+    const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
+    const float2 mx = make_float2(fmaxf(ax0, ay0), fmaxf(ax1, ay1));
+    const float2 mn = make_float2(fminf(ax0, ay0), fminf(ax1, ay1));
+    const float2 t = mul2(mn, make_float2(rcp_approx(mx.x), rcp_approx(mx.y)));
+    const float2 t2 = mul2(t, t);
+    // coefficients of t^15, t^13, ..., t^1
+    float2 p = f2(-0.004054575f);
+    p = fma2(p, t2, f2(0.021862987f));
+    p = fma2(p, t2, f2(-0.05591237f));
+    p = fma2(p, t2, f2(0.09642201f));
+    p = fma2(p, t2, f2(-0.1390863f));
+    p = fma2(p, t2, f2(0.19946566f));
+    p = fma2(p, t2, f2(-0.3332986f));
+    p = fma2(p, t2, f2(0.99999934f));
+    float2 r = mul2(p, t);
+    r = sel2(ay0 > ax0, ay1 > ax1, rsub2(r, f2(1.57079632679489662f)), r);
+    r = sel2(x.x < 0.0f, x.y < 0.0f, rsub2(r, f2(kPi)), r);
+    return make_float2(copysignf(r.x, y.x), copysignf(r.y, y.y));
 }
 
 // Wraps an angle from (-3 pi, 3 pi) into [-pi, pi].
@@ -118,85 +164,106 @@ struct UpdateConst {
     float q, inv_q, two_pi_q, J;
 };
 
-struct UpdateOut {
-    float phi;      // new angle
-    float R;        // local field length |sum_j exp(i q phi_j)|
-    float x_new;    // q * phi_new - Psi (site energy = -J R cos(x_new))
-    bool accepted;
+// Per pair: the uniforms of Alg. 1 steps 2 and 6 come from one Philox block,
+// words (0, 1) for the even realisation and (2, 3) for the odd one, as
+// u = (w >> 8) 2^-24.  The proposal uses (u - 1/2) alpha = (w >> 8 - 2^23)
+// (alpha 2^-24) (the same product, the power of two being exact).
+struct PairRand {
+    float2 um;  // (w >> 8) - 2^23 of both realisations (exact integers)
+    float2 r;   // acceptance uniforms
+};
+__device__ __forceinline__ PairRand pair_uniforms(uint4 w) {
+    PairRand o;
+    o.um = add2(make_float2((float)(w.x >> 8), (float)(w.z >> 8)), f2(-8388608.0f));
+    o.r = mul2(make_float2((float)(w.y >> 8), (float)(w.w >> 8)), f2(0x1p-24f));
+    return o;
+}
+
+struct PairOut {
+    float2 phi;     // new angles
+    float2 e;       // site energies after the update (when requested)
+    bool acc0, acc1;
 };
 
-// The restricted Metropolis half of Alg. 1 (steps 2-6) for a spin at phi1
-// (after over-relaxation) in the field of length R and angle Psi:
+// Alg. 1 steps 2-6 for both realisations of a pair whose spins sit at phi1
+// (after over-relaxation):
 //  2-3. proposal phi'' = (phi1 + alpha (u - 1/2)) mod 2 pi, alpha = 2 pi / a;
 //  4. dH = -J R [cos(q phi'' - Psi) - cos(q phi1 - Psi)]
 //        = 2 J R sin(x + h) sin(h), x = q phi1 - Psi, h = q (phi'' - phi1) / 2
 //     (product form: no cancellation for small steps);
-//  5-6. accept iff r < exp(-dH / T) (always when dH <= 0).
-__device__ __forceinline__ UpdateOut metropolis_step(float phi1, float Psi, float R, uint32_t wu,
-                                                     uint32_t wr, const UpdateConst& k,
-                                                     float alpha, float invT) {
-    const float u = u24(wu);
-    const float r = u24(wr);
-    float phi2 = fmaf(alpha, u - 0.5f, phi1);
-    if (phi2 < 0.0f) phi2 += kTwoPi;
-    else if (phi2 >= kTwoPi) phi2 -= kTwoPi;
-    const float x = fmaf(k.q, phi1, -Psi);
-    const float h = 0.5f * k.q * (phi2 - phi1);
+//  5-6. accept iff r < exp(-dH / T) (dH <= 0 gives exp >= 1 > r: always).
+// alpha_s = alpha 2^-24; c_acc = log2(e) / T (so that exp(-dH/T) = 2^(-dH c_acc)).
+template <bool ENERGY>
+__device__ __forceinline__ PairOut metropolis_pair(float2 phi1, float2 mPsi, float2 R,
+                                                   const PairRand& u, const UpdateConst& k,
+                                                   float2 alpha_s, float c_acc) {
+    float2 phi2 = fma2(alpha_s, u.um, phi1);
+    // mod 2 pi: phi2 lies in (-pi, 3 pi)
+    phi2 = sel2(phi2.x < 0.0f, phi2.y < 0.0f, add2(phi2, f2(kTwoPi)),
+                sel2(phi2.x >= kTwoPi, phi2.y >= kTwoPi, add2(phi2, f2(-kTwoPi)), phi2));
+    const float2 x = fma2(f2(k.q), phi1, mPsi);
+    const float2 h = mul2(f2(0.5f * k.q), rsub2(phi1, phi2));
     // x + h lies in (-3 pi/2, 5 pi/2): the hardware sine reduces that range itself
-    const float s1 = __sinf(x + h);
-    const float s2 = sin_taylor(h);
-    const float dH = 2.0f * k.J * R * s1 * s2;
-    const bool acc = (dH <= 0.0f) || (r < __expf(-dH * invT));
-    UpdateOut o;
-    o.phi = acc ? phi2 : phi1;
-    o.R = R;
-    o.x_new = acc ? x + 2.0f * h : x;
-    o.accepted = acc;
+    const float2 xh = add2(x, h);
+    const float2 s1 = make_float2(sin_approx(xh.x), sin_approx(xh.y));
+    const float2 s2 = sin_taylor2(h);
+    const float2 dH = mul2(mul2(mul2(f2(2.0f * k.J), R), s1), s2);
+    const float2 arg = mul2(dH, f2(-c_acc));
+    PairOut o;
+    o.acc0 = u.r.x < ex2_approx(arg.x);
+    o.acc1 = u.r.y < ex2_approx(arg.y);
+    o.phi = sel2(o.acc0, o.acc1, phi2, phi1);
+    if (ENERGY) {
+        // site energy -J R cos(x_new), x_new = x + 2h if accepted
+        const float2 xn = sel2(o.acc0, o.acc1, fma2(f2(2.0f), h, x), x);
+        o.e = mul2(mul2(f2(-k.J), R),
+                   make_float2(cos_approx(wrap_pi(xn.x)), cos_approx(wrap_pi(xn.y))));
+    }
     return o;
 }
 
-// One application of Alg. 1 to a gap site with angle phi whose neighbours
-// give the field (C, S) = sum_j (cos q phi_j, sin q phi_j): over-relaxation
-// (Eq. over-relax, q-consistent): Psi = atan2(S, C), theta' = (2 Psi - q phi)
-// mod 2 pi, phi' = theta'/q if theta' < 2 pi q (else phi' = phi); then the
-// restricted Metropolis step.
-__device__ __forceinline__ UpdateOut hybrid_update(float phi, float C, float S, uint32_t wu,
-                                                   uint32_t wr, const UpdateConst& k,
-                                                   float alpha, float invT) {
-    const float R2 = fmaf(C, C, S * S);
-    float Psi = 0.0f;
-    float phi1 = phi;
-    float R = 0.0f;
-    if (R2 > kFieldEps2) {
-        Psi = atan2_poly(S, C);
-        R = R2 * rsqrtf(R2);
-        float t = fmaf(2.0f, Psi, -k.q * phi);
-        t = fmaf(-kTwoPi, floorf(t * kInvTwoPi), t);
-        if (t >= 0.0f && t < k.two_pi_q) phi1 = t * k.inv_q;
-    }
-    return metropolis_step(phi1, Psi, R, wu, wr, k, alpha, invT);
+// One application of Alg. 1 to the gap site of both realisations of a pair,
+// with angles phi and neighbour fields (C, S) = sum_j (cos q phi_j, sin q phi_j):
+// over-relaxation (Eq. over-relax, q-consistent): Psi = atan2(S, C),
+// theta' = (2 Psi - q phi) mod 2 pi, phi' = theta'/q if theta' < 2 pi q (else
+// phi' = phi; no reflection when |field| < 1e-12); then the restricted
+// Metropolis step.
+template <bool ENERGY>
+__device__ __forceinline__ PairOut hybrid_pair(float2 phi, float2 C, float2 S, const PairRand& u,
+                                               const UpdateConst& k, float2 alpha_s, float c_acc) {
+    const float2 R2 = fma2(C, C, mul2(S, S));
+    const bool f0 = R2.x > kFieldEps2, f1 = R2.y > kFieldEps2;
+    const float2 Psi = sel2(f0, f1, atan2_pair(S, C), f2(0.0f));
+    const float2 R = sel2(f0, f1, mul2(R2, make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y))),
+                          f2(0.0f));
+    float2 t = fma2(f2(2.0f), Psi, mul2(f2(-k.q), phi));
+    t = fma2(f2(-kTwoPi), floor2(mul2(t, f2(kInvTwoPi))), t);
+    const float2 ref = mul2(t, f2(k.inv_q));
+    const float2 phi1 = sel2(f0 && t.x >= 0.0f && t.x < k.two_pi_q,
+                             f1 && t.y >= 0.0f && t.y < k.two_pi_q, ref, phi);
+    return metropolis_pair<ENERGY>(phi1, mul2(Psi, f2(-1.0f)), R, u, k, alpha_s, c_acc);
 }
 
 // Alg. 1 with the over-relaxation formula as printed (Eq. over-relax with the
 // q = 1 field (C1, S1) = sum_j (cos phi_j, sin phi_j)): phi' = (2 Phi - phi)
 // mod 2 pi, Phi = atan2(S1, C1), always applied; the Metropolis step still
 // uses the MPR energy through its field (C, S).
-__device__ __forceinline__ UpdateOut literal_update(float phi, float C, float S, float C1, float S1,
-                                                    uint32_t wu, uint32_t wr, const UpdateConst& k,
-                                                    float alpha, float invT) {
-    const float R2 = fmaf(C, C, S * S);
-    float Psi = 0.0f, R = 0.0f;
-    if (R2 > kFieldEps2) {
-        Psi = atan2_poly(S, C);
-        R = R2 * rsqrtf(R2);
-    }
-    float phi1 = phi;
-    if (fmaf(C1, C1, S1 * S1) > kFieldEps2) {
-        float t = fmaf(2.0f, atan2_poly(S1, C1), -phi);
-        phi1 = fmaf(-kTwoPi, floorf(t * kInvTwoPi), t);
-        if (phi1 >= kTwoPi || phi1 < 0.0f) phi1 = 0.0f;
-    }
-    return metropolis_step(phi1, Psi, R, wu, wr, k, alpha, invT);
+template <bool ENERGY>
+__device__ __forceinline__ PairOut literal_pair(float2 phi, float2 C, float2 S, float2 C1,
+                                                float2 S1, const PairRand& u, const UpdateConst& k,
+                                                float2 alpha_s, float c_acc) {
+    const float2 R2 = fma2(C, C, mul2(S, S));
+    const bool f0 = R2.x > kFieldEps2, f1 = R2.y > kFieldEps2;
+    const float2 Psi = sel2(f0, f1, atan2_pair(S, C), f2(0.0f));
+    const float2 R = sel2(f0, f1, mul2(R2, make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y))),
+                          f2(0.0f));
+    const float2 Q2 = fma2(C1, C1, mul2(S1, S1));
+    const bool g0 = Q2.x > kFieldEps2, g1 = Q2.y > kFieldEps2;
+    float2 t = fma2(f2(2.0f), atan2_pair(S1, C1), mul2(f2(-1.0f), phi));
+    t = fma2(f2(-kTwoPi), floor2(mul2(t, f2(kInvTwoPi))), t);
+    t = sel2(t.x >= kTwoPi || t.x < 0.0f, t.y >= kTwoPi || t.y < 0.0f, f2(0.0f), t);
+    const float2 phi1 = sel2(g0, g1, t, phi);
+    return metropolis_pair<ENERGY>(phi1, mul2(Psi, f2(-1.0f)), R, u, k, alpha_s, c_acc);
 }
 
 // Alg. 1 with the GMRF pair interaction of Sec. 4.3 (every bond costs
@@ -205,33 +272,31 @@ __device__ __forceinline__ UpdateOut literal_update(float phi, float C, float S,
 // it, phi' = 2m - phi, kept inside [0, 2 pi); the proposal and acceptance are
 // those of the MPR step, with
 // dH = J n (phi'' - phi')(phi'' + phi' - 2m) / (2 pi^2) (a product: no cancellation).
-__device__ __forceinline__ UpdateOut gmrf_update(float phi, float m, float n, uint32_t wu,
-                                                 uint32_t wr, float J, float alpha, float invT) {
-    const float t = fmaf(2.0f, m, -phi);
-    const float phi1 = (t >= 0.0f && t < kTwoPi) ? t : phi;
-    const float u = u24(wu);
-    const float r = u24(wr);
-    float phi2 = fmaf(alpha, u - 0.5f, phi1);
-    if (phi2 < 0.0f) phi2 += kTwoPi;
-    else if (phi2 >= kTwoPi) phi2 -= kTwoPi;
+// sum = sum of the neighbour angles, n their number (m = sum (1/n)).
+template <bool ENERGY>
+__device__ __forceinline__ PairOut gmrf_pair(float2 phi, float2 sum, float n, const PairRand& u,
+                                             float J, float2 alpha_s, float c_acc) {
+    const float2 m = mul2(sum, f2(__frcp_rn(n)));
+    const float2 t = fma2(f2(2.0f), m, mul2(f2(-1.0f), phi));
+    const float2 phi1 = sel2(t.x >= 0.0f && t.x < kTwoPi, t.y >= 0.0f && t.y < kTwoPi, t, phi);
+    float2 phi2 = fma2(alpha_s, u.um, phi1);
+    phi2 = sel2(phi2.x < 0.0f, phi2.y < 0.0f, add2(phi2, f2(kTwoPi)),
+                sel2(phi2.x >= kTwoPi, phi2.y >= kTwoPi, add2(phi2, f2(-kTwoPi)), phi2));
     constexpr float kInvTwoPi2 = 0.050660591821168885f;  // 1 / (2 pi^2)
-    const float dH = J * n * kInvTwoPi2 * (phi2 - phi1) * ((phi2 + phi1) - 2.0f * m);
-    const bool acc = (dH <= 0.0f) || (r < __expf(-dH * invT));
-    UpdateOut o;
-    o.phi = acc ? phi2 : phi1;
-    o.R = 0.0f;
-    o.x_new = 0.0f;
-    o.accepted = acc;
+    const float2 d = rsub2(phi1, phi2);
+    const float2 s = fma2(f2(-2.0f), m, add2(phi2, phi1));
+    const float2 dH = mul2(mul2(f2(J * n * kInvTwoPi2), d), s);
+    const float2 arg = mul2(dH, f2(-c_acc));
+    PairOut o;
+    o.acc0 = u.r.x < ex2_approx(arg.x);
+    o.acc1 = u.r.y < ex2_approx(arg.y);
+    o.phi = sel2(o.acc0, o.acc1, phi2, phi1);
+    if (ENERGY) o.e = f2(0.0f);  // GMRF bond energies are summed by the caller
     return o;
 }
 
 __device__ __forceinline__ float gmrf_bond(float d) {
     return fmaf(d * d, 0.050660591821168885f, -1.0f);
-}
-
-// Energy of a site after its update: -J R cos(x_new).
-__device__ __forceinline__ float site_energy_after(const UpdateOut& o, float J) {
-    return -J * o.R * __cosf(wrap_pi(o.x_new));
 }
 
 // --------------------------------------------------------- reductions

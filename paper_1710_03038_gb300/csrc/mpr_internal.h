@@ -76,7 +76,9 @@ struct SweepArgs {
     const TileDesc* tiles;      // tiled path
     const uint32_t* slot_pos;   // tiled: (y << 16) | x per slot, 0xFFFFFFFF for padding
     const uint2* slot_ref;      // tiled: table entries of the slot's gap neighbours (u16 x 4)
-    const float2* slot_cs;      // tiled: sum over the slot's sample neighbours of (cos, sin) q phi
+    const float4* slot_cs;      // tiled: the slot's sample field: sum over its sample neighbours of
+                                // (cos q phi, sin q phi, cos phi, sin phi); GMRF: (sum phi, number
+                                // of existing neighbours, 0, 0)
     const int2* halo;           // tiled: [tile][2][cap] (slot, cs index)
     const float* samp;          // tiled: sample angle per site (>= 0) or -1 at gaps
     float* state;
@@ -110,6 +112,8 @@ cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tile_x, int t
                               cudaStream_t s, bool setup_only = false);
 cudaError_t launch_plain_pass(const SweepArgs& a, int max_Lx, int max_Ly, cudaStream_t s);
 bool tiled_config_supported(int tile_x, int tile_y);
+// the printed over-relaxation and the GMRF model run with 16 x 16 tiles
+bool tiled_model_supported(int tile_x, int tile_y, int flags);
 
 // tile-table construction (tiled path)
 cudaError_t launch_tile_count(const ImgDev* img, const TileDesc* tiles, int n_tiles,
@@ -122,12 +126,13 @@ cudaError_t launch_tile_fill(const ImgDev* img, const TileDesc* tiles, int n_til
 // colour (up, down, left, right; 0 = not a gap) and its sample field
 cudaError_t launch_tile_const(const ImgDev* img, const TileDesc* tiles, int n_tiles, int tile_x,
                               int tile_y, const uint32_t* slot_pos, const int2* halo, int halo_cap,
-                              const float* samp, float q, uint2* slot_ref, float2* slot_cs,
-                              cudaStream_t s);
+                              const float* samp, float q, int gmrf, uint2* slot_ref,
+                              float4* slot_cs, cudaStream_t s);
 // Shared memory of a colour-pass block: fixed part plus `per_entry` bytes per
 // table entry; `blocks` = the most blocks an SM can hold by their threads.
-void tiled_smem_shape(int tile_x, int tile_y, int chain_group, size_t* fixed, size_t* per_entry,
-                      int* blocks);
+// flags: the model bits of SweepFlags (kLiteralOR, kGMRF).
+void tiled_smem_shape(int tile_x, int tile_y, int chain_group, int flags, size_t* fixed,
+                      size_t* per_entry, int* blocks);
 
 // float offset of gap slot k (tiled) or site k (plain) of a realisation
 __host__ __device__ inline long long state_index(const ImgDev& I, int chain, long long k) {

@@ -83,9 +83,9 @@ __global__ void math_probe_kernel(int fn, int n, const float* a, const float* b,
     if (i >= n) return;
     float v = 0.0f;
     switch (fn) {
-        case 0: v = atan2_poly(a[i], b[i]); break;
+        case 0: v = atan2_pair(f2(a[i]), f2(b[i])).x; break;
         case 1: v = atan2f(a[i], b[i]); break;
-        case 2: v = sin_taylor(a[i]); break;
+        case 2: v = sin_taylor2(f2(a[i])).x; break;
         default: v = sinf(a[i]); break;
     }
     out[i] = v;

@@ -10,6 +10,10 @@ namespace mpr {
 cudaError_t launch_tiled_32x16(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only);
 cudaError_t launch_tiled_16x16(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only);
 cudaError_t launch_tiled_32x32(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only);
+cudaError_t launch_tiled_16x16_lit(const SweepArgs& a, int n_tiles, cudaStream_t s,
+                                   bool setup_only);
+cudaError_t launch_tiled_16x16_gmrf(const SweepArgs& a, int n_tiles, cudaStream_t s,
+                                    bool setup_only);
 
 namespace {
 
@@ -117,12 +121,14 @@ __global__ void tile_halo_kernel(const ImgDev* img, TileDesc* tiles, const int* 
 // Per-slot constants of the colour passes, built once per batch: for every
 // gap site of colour c, the table entries of its four neighbours in the pass
 // of colour c (interior other-colour cells 1 + j, ring cells 1 + n_oth + k,
-// 0 where the neighbour is a sample or outside) and the sum over its sample
-// neighbours of (cos q phi, sin q phi) in the order up, down, left, right.
+// 0 where the neighbour is a sample or outside) and its sample field, summed
+// over its sample neighbours in the order up, down, left, right:
+// (cos q phi, sin q phi, cos phi, sin phi), or for the GMRF model
+// (sum of the sample angles, number of existing neighbours, 0, 0).
 __global__ void tile_const_kernel(const ImgDev* img, const TileDesc* tiles, int tx, int ty,
                                   const uint32_t* slot_pos, const int2* halo, int halo_cap,
-                                  const float* samp_all, float q, uint2* slot_ref,
-                                  float2* slot_cs) {
+                                  const float* samp_all, float q, int gmrf, uint2* slot_ref,
+                                  float4* slot_cs) {
     extern __shared__ uint16_t cellmap[];  // [(ty + 2) * (tx + 2)]
     const TileDesc T = tiles[blockIdx.x];
     const ImgDev& I = img[T.img];
@@ -146,7 +152,7 @@ __global__ void tile_const_kernel(const ImgDev* img, const TileDesc* tiles, int 
             const uint32_t p = spos[T.off[c] + j];
             const int X = (int)(p & 0xFFFFu), Y = (int)(p >> 16);
             const int xx = X - T.x0 + 1, yy = Y - T.y0 + 1;
-            float2 f = make_float2(0.0f, 0.0f);
+            float4 f = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             uint32_t ref[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {  // up, down, left, right
@@ -155,12 +161,20 @@ __global__ void tile_const_kernel(const ImgDev* img, const TileDesc* tiles, int 
                 const int nx = X + dx, ny = Y + dy;
                 ref[m] = 0u;
                 if (nx < 0 || nx >= I.Lx || ny < 0 || ny >= I.Ly) continue;
+                if (gmrf) f.y += 1.0f;
                 const float v = samp[(long long)ny * I.Lx + nx];
                 if (v >= 0.0f) {
-                    float sn, cs;
-                    __sincosf(q * v, &sn, &cs);
-                    f.x += cs;
-                    f.y += sn;
+                    if (gmrf) {
+                        f.x += v;
+                    } else {
+                        float sn, cs;
+                        __sincosf(q * v, &sn, &cs);
+                        f.x += cs;
+                        f.y += sn;
+                        __sincosf(v, &sn, &cs);
+                        f.z += cs;
+                        f.w += sn;
+                    }
                 } else {
                     ref[m] = cellmap[(yy + dy) * ew + (xx + dx)];
                 }
@@ -174,24 +188,40 @@ __global__ void tile_const_kernel(const ImgDev* img, const TileDesc* tiles, int 
 
 }  // namespace
 
-void tiled_smem_shape(int tx, int ty, int chain_group, size_t* fixed, size_t* per_entry,
-                      int* blocks) {
-    const int P = tiled::pairs_for_group(chain_group);
-    *per_entry = sizeof(float4) * P;
-    if (tx == 32 && ty == 16) {
-        *fixed = tiled::Cfg<32, 16, 8>::off_tab;
-        *blocks = 1024 / tiled::Cfg<32, 16, 8>::NT;
+void tiled_smem_shape(int tx, int ty, int chain_group, int flags, size_t* fixed,
+                      size_t* per_entry, int* blocks) {
+    using namespace tiled;
+    const int P = pairs_for_group(chain_group);
+    if (flags & kGMRF) {
+        *per_entry = (size_t)Cell<kModelGMRF>::bytes * P;
+        *fixed = Cfg<16, 16, 4, kModelGMRF>::off_tab;
+        *blocks = 1024 / Cfg<16, 16, 4, kModelGMRF>::NT;
+    } else if (flags & kLiteralOR) {
+        *per_entry = (size_t)Cell<kModelLIT>::bytes * P;
+        *fixed = Cfg<16, 16, 4, kModelLIT>::off_tab;
+        *blocks = 1024 / Cfg<16, 16, 4, kModelLIT>::NT;
+    } else if (tx == 32 && ty == 16) {
+        *per_entry = (size_t)Cell<kModelMPR>::bytes * P;
+        *fixed = Cfg<32, 16, 8, kModelMPR>::off_tab;
+        *blocks = 1024 / Cfg<32, 16, 8, kModelMPR>::NT;
     } else if (tx == 32 && ty == 32) {
-        *fixed = tiled::Cfg<32, 32, 8>::off_tab;
-        *blocks = 1024 / tiled::Cfg<32, 32, 8>::NT;
+        *per_entry = (size_t)Cell<kModelMPR>::bytes * P;
+        *fixed = Cfg<32, 32, 8, kModelMPR>::off_tab;
+        *blocks = 1024 / Cfg<32, 32, 8, kModelMPR>::NT;
     } else {
-        *fixed = tiled::Cfg<16, 16, 4>::off_tab;
-        *blocks = 1024 / tiled::Cfg<16, 16, 4>::NT;
+        *per_entry = (size_t)Cell<kModelMPR>::bytes * P;
+        *fixed = Cfg<16, 16, 4, kModelMPR>::off_tab;
+        *blocks = 1024 / Cfg<16, 16, 4, kModelMPR>::NT;
     }
 }
 
 bool tiled_config_supported(int tx, int ty) {
     return (tx == 32 && ty == 16) || (tx == 16 && ty == 16) || (tx == 32 && ty == 32);
+}
+
+bool tiled_model_supported(int tx, int ty, int flags) {
+    if (flags & (kGMRF | kLiteralOR)) return tx == 16 && ty == 16;
+    return tiled_config_supported(tx, ty);
 }
 
 cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, cudaStream_t s,
@@ -200,6 +230,9 @@ cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, c
         a.chain_end <= a.chain0 || a.chain_end > a.n_chains ||
         (a.chain_group % 2 != 0 && a.chain_group < a.chain_end - a.chain0))
         return cudaErrorInvalidValue;
+    if (!tiled_model_supported(tx, ty, a.flags)) return cudaErrorInvalidValue;
+    if (a.flags & kGMRF) return launch_tiled_16x16_gmrf(a, n_tiles, s, setup_only);
+    if (a.flags & kLiteralOR) return launch_tiled_16x16_lit(a, n_tiles, s, setup_only);
     if (tx == 32 && ty == 16) return launch_tiled_32x16(a, n_tiles, s, setup_only);
     if (tx == 16 && ty == 16) return launch_tiled_16x16(a, n_tiles, s, setup_only);
     if (tx == 32 && ty == 32) return launch_tiled_32x32(a, n_tiles, s, setup_only);
@@ -227,11 +260,11 @@ cudaError_t launch_tile_fill(const ImgDev* img, const TileDesc* tiles, int n_til
 
 cudaError_t launch_tile_const(const ImgDev* img, const TileDesc* tiles, int n_tiles, int tx, int ty,
                               const uint32_t* slot_pos, const int2* halo, int halo_cap,
-                              const float* samp, float q, uint2* slot_ref, float2* slot_cs,
-                              cudaStream_t s) {
+                              const float* samp, float q, int gmrf, uint2* slot_ref,
+                              float4* slot_cs, cudaStream_t s) {
     const size_t smem = sizeof(uint16_t) * (tx + 2) * (ty + 2);
     tile_const_kernel<<<n_tiles, 256, smem, s>>>(img, tiles, tx, ty, slot_pos, halo, halo_cap,
-                                                 samp, q, slot_ref, slot_cs);
+                                                 samp, q, gmrf, slot_ref, slot_cs);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 namespace mpr {
 
 cudaError_t launch_tiled_16x16(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
-    return tiled::launch_shape<16, 16, 4>(a, n_tiles, s, setup_only);
+    return tiled::launch_shape<16, 16, 4, tiled::kModelMPR>(a, n_tiles, s, setup_only);
 }
 
 }  // namespace mpr

@@ -4,7 +4,7 @@
 namespace mpr {
 
 cudaError_t launch_tiled_32x32(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
-    return tiled::launch_shape<32, 32, 8>(a, n_tiles, s, setup_only);
+    return tiled::launch_shape<32, 32, 8, tiled::kModelMPR>(a, n_tiles, s, setup_only);
 }
 
 }  // namespace mpr
