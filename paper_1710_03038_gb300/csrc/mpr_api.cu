@@ -65,9 +65,10 @@ struct Geometry {
 };
 
 // Floats per slot of the state buffer: the tiled layout interleaves the
-// chains, rounded up to an even count so that chain pairs are aligned float2.
+// chains, rounded up to a multiple of 4 so that every chain group's part of a
+// slot is a 16-byte aligned row (bulk copies) and chain pairs are float2.
 long long state_chains(const Geometry& g) {
-    return g.path == MPR_PATH_TILED ? (long long)((g.n_chains + 1) & ~1) : (long long)g.n_chains;
+    return g.path == MPR_PATH_TILED ? (long long)((g.n_chains + 3) & ~3) : (long long)g.n_chains;
 }
 
 void make_geometry(Geometry& g, int n_img, const int* Lx, const int* Ly, int n_chains, int path,
@@ -681,18 +682,17 @@ int model_flags(const mpr_params& p) {
     return (p.literal_or ? kLiteralOR : 0) | (p.model == MPR_MODEL_GMRF ? kGMRF : 0);
 }
 
-// Chains per thread block of the tiled pass (even, or covering every chain;
-// at most 32).  Automatic: the largest power of two up to 32 that still gives
-// at least four blocks per SM (152 SMs); on the 256^2 x 16 temperature
-// lattices that is 4 (measured 7.3 ms per estimate against 9.3 ms with 2 and
-// 7.5 ms with 8).
+// Chains per thread block of the tiled pass (a multiple of 4, or covering
+// every chain; at most 32).  Automatic: the largest power of two from 4 up to
+// 32 that still gives at least four blocks per SM (152 SMs); on the
+// 256^2 x 16 temperature lattices that is 4.
 int pick_chain_group(const mpr_ctx* c) {
     if (c->g.path != MPR_PATH_TILED) return 1;
     const int n = c->g.n_chains;
     if (c->p.chain_group > 0) return std::min(c->p.chain_group, 32);
     const long long target = 152LL * 4;
     const long long tiles = std::max(1, c->g.n_tiles);
-    int cg = 2;
+    int cg = 4;
     while (cg < 32 && cg < n && tiles * ((n + 2 * cg - 1) / (2 * cg)) >= target) cg *= 2;
     return cg >= n ? n : cg;
 }
@@ -723,14 +723,12 @@ int chain_ranges(const mpr_ctx* c, ChainRange out[2]) {
 // cut the occupancy of every block.  Without heavy tiles a pass is one launch.
 mpr_status split_tiles(mpr_ctx* c, const std::vector<TileDesc>& tiles, cudaStream_t s) {
     const Geometry& g = c->g;
-    size_t fixed = 0, per = 0;
-    int blocks = 1, dev = 0, sm_bytes = 0, reserved = 0;
-    tiled_smem_shape(g.tx, g.ty, pick_chain_group(c), model_flags(c->p), &fixed, &per, &blocks);
+    const int cg = pick_chain_group(c), flags = model_flags(c->p);
+    int dev = 0, sm_bytes = 0, reserved = 0;
     MPR_CUDA(cudaGetDevice(&dev));
     MPR_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     MPR_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
-    const size_t budget = (size_t)sm_bytes / (size_t)blocks - (size_t)reserved;
-    const int cap = budget > fixed + per ? (int)((budget - fixed) / per) : 1;
+    const size_t budget = (size_t)sm_bytes / tiled_blocks_per_sm(g.tx, g.ty) - (size_t)reserved;
     const int n = g.n_tiles;
     std::vector<int> list(2 * (size_t)n);
     bool split = false;
@@ -740,7 +738,7 @@ mpr_status split_tiles(mpr_ctx* c, const std::vector<TileDesc>& tiles, cudaStrea
         for (int t = 0; t < n; ++t) {
             const int e = tiles[t].cnt[col ^ 1] + tiles[t].halo_cnt[col] + 1;
             gmax = std::max(gmax, e);
-            if (e <= cap) {
+            if (tiled_pass_smem(g.tx, g.ty, e, cg, flags) <= budget) {
                 list[(size_t)col * n + nl++] = t;
                 glight = std::max(glight, e);
             } else {
@@ -970,6 +968,12 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
     MPR_CUDA(cudaMemcpyAsync(c->d_img, c->h_img.data(), sizeof(ImgDev) * n_img,
                              cudaMemcpyHostToDevice, s));
     if (tiled) {
+        for (TileDesc& t : tiles) {
+            const ImgDev& I = c->h_img[t.img];
+            t.cp = (int)I.sstride;
+            t.state_off = I.state_off;
+            t.slot_off = I.slot_off;
+        }
         MPR_CUDA(cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(TileDesc) * g.n_tiles,
                                  cudaMemcpyHostToDevice, s));
         MPR_CUDA(cudaMemsetAsync(c->d_slot_pos, 0xFF, sizeof(uint32_t) * c->L.n_slots, s));
@@ -1096,13 +1100,15 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
                 a.tile_list = nl < nt ? c->d_tile_list + (size_t)colour * nt : nullptr;
                 if (nl > 0) {  // the light tiles (all of them without a heavy launch)
                     a.tile_base = 0;
+                    a.n_list = nl;
                     a.gt = nl < nt ? c->gt_light[colour] : c->gt[colour];
-                    e = launch_tiled_pass(a, nl, c->g.tx, c->g.ty, s);
+                    e = launch_tiled_pass(a, c->g.tx, c->g.ty, s);
                 }
                 if (e == cudaSuccess && nl < nt) {
                     a.tile_base = nl;
+                    a.n_list = nt - nl;
                     a.gt = c->gt[colour];
-                    e = launch_tiled_pass(a, nt - nl, c->g.tx, c->g.ty, s);
+                    e = launch_tiled_pass(a, c->g.tx, c->g.ty, s);
                 }
                 if (e == cudaSuccess && n_cr > 1) {  // the remaining chains, every tile
                     a.chain0 = cr[1].chain0;
@@ -1110,8 +1116,9 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
                     a.chain_group = cr[1].group;
                     a.tile_list = nullptr;
                     a.tile_base = 0;
+                    a.n_list = nt;
                     a.gt = c->gt[colour];
-                    e = launch_tiled_pass(a, nt, c->g.tx, c->g.ty, s);
+                    e = launch_tiled_pass(a, c->g.tx, c->g.ty, s);
                 }
             }
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
@@ -1156,7 +1163,7 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
                     a.chain0 = cr[r].chain0;
                     a.chain_end = cr[r].chain_end;
                     a.chain_group = cr[r].group;
-                    MPR_CUDA(launch_tiled_pass(a, 0, c->g.tx, c->g.ty, s, true));
+                    MPR_CUDA(launch_tiled_pass(a, c->g.tx, c->g.ty, s, true));
                 }
             }
             MPR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1271,10 +1278,11 @@ mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly,
     mpr_ctx* c = new (std::nothrow) mpr_ctx();
     if (!c) return fail(MPR_ERR_INVALID_ARG, "out of host memory");
     c->p = *p;
-    if (p->chain_group > 0 && (p->chain_group & 1) && p->chain_group < n_chains) {
+    if (p->chain_group > 0 && (p->chain_group & 3) && p->chain_group < n_chains) {
         delete c;
-        return fail(MPR_ERR_INVALID_ARG, "chain_group must be even or cover every chain "
-                                         "(realisations 2m and 2m+1 share random numbers)");
+        return fail(MPR_ERR_INVALID_ARG, "chain_group must be a multiple of 4 or cover every "
+                                         "chain (pairs share random numbers; rows are 16-byte "
+                                         "aligned)");
     }
     mpr_default_T_opts(&c->topt);
     if (T_opts) c->topt = *T_opts;
@@ -1427,7 +1435,8 @@ mpr_status mpr_autotune(int n_img, const int* Lx, const int* Ly, int n_chains, m
                 T[i] = std::min(10.0, std::max(1e-4, 4.0 * (e_s + p->J)));
             }
             MPR_TRY(mpr_set_T(&c, T.data(), stream));
-            MPR_TRY(run_sweeps(&c, 1, MPR_EQUIL, 0, false, false, s));
+            // a candidate whose buffers do not fit the device is skipped
+            if (run_sweeps(&c, 1, MPR_EQUIL, 0, false, false, s) != MPR_OK) continue;
             cudaEvent_t e0, e1;
             MPR_CUDA(cudaEventCreate(&e0));
             MPR_CUDA(cudaEventCreate(&e1));

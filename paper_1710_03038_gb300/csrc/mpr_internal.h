@@ -14,14 +14,21 @@
 namespace mpr {
 
 // Tile of the tiled path.  Origins are multiples of the (even) tile sizes,
-// so the colour of extended-tile cell (xx, yy) is (xx + yy) & 1.
+// so the colour of extended-tile cell (xx, yy) is (xx + yy) & 1.  The record
+// is 16 words (64 bytes) so that 16 lanes load it in one access; it repeats
+// the image offsets the colour pass needs to address the tile's state.
 struct TileDesc {
     int img;
     int x0, y0;
+    int cp;           // floats per slot of the image's state (chains rounded up to 4)
     int off[2];       // slot offset of the colour-c gap segment inside the image's slot space
     int cnt[2];       // gap sites of colour c in the tile
     int halo_cnt[2];  // other-colour gap sites in the 1-ring seen by the colour-c pass
+    long long state_off;  // float offset of the image's state
+    long long slot_off;   // offset of the image in the slot arrays
+    int pad[2];
 };
+static_assert(sizeof(TileDesc) == 64, "tile record: 16 words");
 
 // Per image, in device memory.
 struct ImgDev {
@@ -95,9 +102,10 @@ struct SweepArgs {
     int colour;
     int flags;
     int halo_cap;
-    int gt;                    // tiled: table entries per chain pair for this pass
-    const int* tile_list;      // tiled: tile of block b is tile_list[tile_base + b] (null: b)
+    int gt;                    // tiled: table entries per chain pair for this pass (largest tile)
+    const int* tile_list;      // tiled: k-th tile of the launch is tile_list[tile_base + k] (null: k)
     int tile_base;
+    int n_list;                // tiled: tiles in the launch
     int n_img;
     uint32_t img_tag;          // OR-ed into the image field of the counter (1 << 30: T lattices)
 };
@@ -108,8 +116,8 @@ mpr_status set_last_error(mpr_status s, const std::string& msg);
 // ---- launchers ------------------------------------------------------------
 // setup_only: set the kernel's attributes without launching (before a capture)
 // (chain_group: even and at most 32, or covering every chain)
-cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tile_x, int tile_y,
-                              cudaStream_t s, bool setup_only = false);
+cudaError_t launch_tiled_pass(const SweepArgs& a, int tile_x, int tile_y, cudaStream_t s,
+                              bool setup_only = false);
 cudaError_t launch_plain_pass(const SweepArgs& a, int max_Lx, int max_Ly, cudaStream_t s);
 bool tiled_config_supported(int tile_x, int tile_y);
 // the printed over-relaxation and the GMRF model run with 16 x 16 tiles
@@ -128,11 +136,12 @@ cudaError_t launch_tile_const(const ImgDev* img, const TileDesc* tiles, int n_ti
                               int tile_y, const uint32_t* slot_pos, const int2* halo, int halo_cap,
                               const float* samp, float q, int gmrf, uint2* slot_ref,
                               float4* slot_cs, cudaStream_t s);
-// Shared memory of a colour-pass block: fixed part plus `per_entry` bytes per
-// table entry; `blocks` = the most blocks an SM can hold by their threads.
-// flags: the model bits of SweepFlags (kLiteralOR, kGMRF).
-void tiled_smem_shape(int tile_x, int tile_y, int chain_group, int flags, size_t* fixed,
-                      size_t* per_entry, int* blocks);
+// Dynamic shared memory of a colour-pass block of tile shape tx x ty for a
+// launch whose largest tile has gt table entries; flags: the model bits of
+// SweepFlags (kLiteralOR, kGMRF).
+size_t tiled_pass_smem(int tx, int ty, int gt, int chain_group, int flags);
+// blocks of the colour pass one SM holds by their threads and registers
+int tiled_blocks_per_sm(int tx, int ty);
 
 // float offset of gap slot k (tiled) or site k (plain) of a realisation
 __host__ __device__ inline long long state_index(const ImgDev& I, int chain, long long k) {

@@ -7,13 +7,11 @@
 
 namespace mpr {
 
-cudaError_t launch_tiled_32x16(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only);
-cudaError_t launch_tiled_16x16(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only);
-cudaError_t launch_tiled_32x32(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only);
-cudaError_t launch_tiled_16x16_lit(const SweepArgs& a, int n_tiles, cudaStream_t s,
-                                   bool setup_only);
-cudaError_t launch_tiled_16x16_gmrf(const SweepArgs& a, int n_tiles, cudaStream_t s,
-                                    bool setup_only);
+cudaError_t launch_tiled_32x16(const SweepArgs& a, cudaStream_t s, bool setup_only);
+cudaError_t launch_tiled_16x16(const SweepArgs& a, cudaStream_t s, bool setup_only);
+cudaError_t launch_tiled_32x32(const SweepArgs& a, cudaStream_t s, bool setup_only);
+cudaError_t launch_tiled_16x16_lit(const SweepArgs& a, cudaStream_t s, bool setup_only);
+cudaError_t launch_tiled_16x16_gmrf(const SweepArgs& a, cudaStream_t s, bool setup_only);
 
 namespace {
 
@@ -188,31 +186,20 @@ __global__ void tile_const_kernel(const ImgDev* img, const TileDesc* tiles, int 
 
 }  // namespace
 
-void tiled_smem_shape(int tx, int ty, int chain_group, int flags, size_t* fixed,
-                      size_t* per_entry, int* blocks) {
+size_t tiled_pass_smem(int tx, int ty, int gt, int chain_group, int flags) {
     using namespace tiled;
     const int P = pairs_for_group(chain_group);
-    if (flags & kGMRF) {
-        *per_entry = (size_t)Cell<kModelGMRF>::bytes * P;
-        *fixed = Cfg<16, 16, 4, kModelGMRF>::off_tab;
-        *blocks = 1024 / Cfg<16, 16, 4, kModelGMRF>::NT;
-    } else if (flags & kLiteralOR) {
-        *per_entry = (size_t)Cell<kModelLIT>::bytes * P;
-        *fixed = Cfg<16, 16, 4, kModelLIT>::off_tab;
-        *blocks = 1024 / Cfg<16, 16, 4, kModelLIT>::NT;
-    } else if (tx == 32 && ty == 16) {
-        *per_entry = (size_t)Cell<kModelMPR>::bytes * P;
-        *fixed = Cfg<32, 16, 8, kModelMPR>::off_tab;
-        *blocks = 1024 / Cfg<32, 16, 8, kModelMPR>::NT;
-    } else if (tx == 32 && ty == 32) {
-        *per_entry = (size_t)Cell<kModelMPR>::bytes * P;
-        *fixed = Cfg<32, 32, 8, kModelMPR>::off_tab;
-        *blocks = 1024 / Cfg<32, 32, 8, kModelMPR>::NT;
-    } else {
-        *per_entry = (size_t)Cell<kModelMPR>::bytes * P;
-        *fixed = Cfg<16, 16, 4, kModelMPR>::off_tab;
-        *blocks = 1024 / Cfg<16, 16, 4, kModelMPR>::NT;
-    }
+    if (flags & kGMRF) return Cfg<16, 16, 4, kModelGMRF>::smem_for(gt, P);
+    if (flags & kLiteralOR) return Cfg<16, 16, 4, kModelLIT>::smem_for(gt, P);
+    if (tx == 32 && ty == 16) return Cfg<32, 16, 8, kModelMPR>::smem_for(gt, P);
+    if (tx == 32 && ty == 32) return Cfg<32, 32, 8, kModelMPR>::smem_for(gt, P);
+    return Cfg<16, 16, 4, kModelMPR>::smem_for(gt, P);
+}
+
+int tiled_blocks_per_sm(int tx, int ty) {
+    using namespace tiled;
+    if (tx == 32) return 1024 / Cfg<32, 16, 8, kModelMPR>::NT;
+    return 1024 / Cfg<16, 16, 4, kModelMPR>::NT;
 }
 
 bool tiled_config_supported(int tx, int ty) {
@@ -224,18 +211,19 @@ bool tiled_model_supported(int tx, int ty, int flags) {
     return tiled_config_supported(tx, ty);
 }
 
-cudaError_t launch_tiled_pass(const SweepArgs& a, int n_tiles, int tx, int ty, cudaStream_t s,
+cudaError_t launch_tiled_pass(const SweepArgs& a, int tx, int ty, cudaStream_t s,
                               bool setup_only) {
-    if (a.chain_group < 1 || a.chain_group > 32 || (a.chain0 & 1) || a.chain0 < 0 ||
+    // chain groups start on a multiple of 4 chains (16-byte aligned rows)
+    if (a.chain_group < 1 || a.chain_group > 32 || (a.chain0 & 3) || a.chain0 < 0 ||
         a.chain_end <= a.chain0 || a.chain_end > a.n_chains ||
-        (a.chain_group % 2 != 0 && a.chain_group < a.chain_end - a.chain0))
+        (a.chain_group % 4 != 0 && a.chain_group < a.chain_end - a.chain0))
         return cudaErrorInvalidValue;
     if (!tiled_model_supported(tx, ty, a.flags)) return cudaErrorInvalidValue;
-    if (a.flags & kGMRF) return launch_tiled_16x16_gmrf(a, n_tiles, s, setup_only);
-    if (a.flags & kLiteralOR) return launch_tiled_16x16_lit(a, n_tiles, s, setup_only);
-    if (tx == 32 && ty == 16) return launch_tiled_32x16(a, n_tiles, s, setup_only);
-    if (tx == 16 && ty == 16) return launch_tiled_16x16(a, n_tiles, s, setup_only);
-    if (tx == 32 && ty == 32) return launch_tiled_32x32(a, n_tiles, s, setup_only);
+    if (a.flags & kGMRF) return launch_tiled_16x16_gmrf(a, s, setup_only);
+    if (a.flags & kLiteralOR) return launch_tiled_16x16_lit(a, s, setup_only);
+    if (tx == 32 && ty == 16) return launch_tiled_32x16(a, s, setup_only);
+    if (tx == 16 && ty == 16) return launch_tiled_16x16(a, s, setup_only);
+    if (tx == 32 && ty == 32) return launch_tiled_32x32(a, s, setup_only);
     return cudaErrorInvalidValue;
 }
 

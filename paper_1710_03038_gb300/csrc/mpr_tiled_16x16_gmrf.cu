@@ -3,9 +3,8 @@
 
 namespace mpr {
 
-cudaError_t launch_tiled_16x16_gmrf(const SweepArgs& a, int n_tiles, cudaStream_t s,
-                                    bool setup_only) {
-    return tiled::launch_shape<16, 16, 4, tiled::kModelGMRF>(a, n_tiles, s, setup_only);
+cudaError_t launch_tiled_16x16_gmrf(const SweepArgs& a, cudaStream_t s, bool setup_only) {
+    return tiled::launch_shape<16, 16, 4, tiled::kModelGMRF>(a, s, setup_only);
 }
 
 }  // namespace mpr

@@ -1,10 +1,10 @@
-// Colour pass for 32 x 32 tiles (8 warps per block).
+// Colour pass for 32 x 32 tiles .
 #include "mpr_tiled_kernel.cuh"
 
 namespace mpr {
 
-cudaError_t launch_tiled_32x32(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
-    return tiled::launch_shape<32, 32, 8, tiled::kModelMPR>(a, n_tiles, s, setup_only);
+cudaError_t launch_tiled_32x32(const SweepArgs& a, cudaStream_t s, bool setup_only) {
+    return tiled::launch_shape<32, 32, 8, tiled::kModelMPR>(a, s, setup_only);
 }
 
 }  // namespace mpr

@@ -6,8 +6,8 @@
 // colour form a contiguous segment of the image's slot space (row-major
 // inside the tile, padded to 4 slots).  The state is slot-major with the
 // realisations interleaved: slot k of chain r sits at k * CP + r, CP being the
-// chain count rounded up to even, so the pair (2m, 2m + 1) of one slot is one
-// aligned float2 and the pairs of a chain group are contiguous.
+// chain count rounded up to a multiple of 4, so the pair (2m, 2m + 1) of one
+// slot is one aligned float2 and the pairs of a chain group are contiguous.
 //
 // Work.  One thread block takes one tile and a group of 2P chains (P pairs).
 // A warp lane is (site s, pair p) with p = lane mod P, so a warp step covers
@@ -115,18 +115,19 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const int p = lane & (P - 1);  // pair of the group (fixed per thread: NT is a multiple of P)
     const int s = lane / P;        // site within a warp step
     const int tile = a.tile_list ? a.tile_list[a.tile_base + blockIdx.x] : (int)blockIdx.x;
-    const TileDesc* Tp = a.tiles + tile;
+    // the tile record carries everything the addresses need (one dependent load)
+    const TileDesc T = a.tiles[tile];
     const int c = a.colour;
     const int oc = c ^ 1;
-    const int n_own = Tp->cnt[c];
+    const int n_own = c ? T.cnt[1] : T.cnt[0];
     const bool energy = (a.flags & kEnergy) != 0;
+    const int n_oth = c ? T.cnt[0] : T.cnt[1];
     // nothing to update and no red-gap / black-sample bond energy to add
-    if (n_own == 0 && !(energy && Tp->cnt[oc] > 0)) return;
-    // tile descriptor as scalars (runtime-indexed struct arrays would live in local memory)
-    const int t_img = Tp->img;
-    const int off_own = Tp->off[c], off_oth = Tp->off[oc];
-    const int n_oth = Tp->cnt[oc];
-    const int n_halo = Tp->halo_cnt[c];
+    if (n_own == 0 && !(energy && n_oth > 0)) return;
+    const int t_img = T.img;
+    const int off_own = c ? T.off[1] : T.off[0], off_oth = c ? T.off[0] : T.off[1];
+    const int n_halo = c ? T.halo_cnt[1] : T.halo_cnt[0];
+    const long long slot_off = T.slot_off;
     const ImgDev& I = a.img[t_img];
     const int r0 = a.chain0 + blockIdx.y * a.chain_group;
     const int ng = min(a.chain_group, a.chain_end - r0);
@@ -136,9 +137,17 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const uint32_t c3 = (uint32_t)t_img | a.img_tag | ((uint32_t)c << 31);
     const uint32_t c2 = (uint32_t)(r0 >> 1) + (uint32_t)p;  // chain >> 1 of the pair
     const UpdateConst uk{a.q, a.inv_q, a.two_pi_q, a.J};
-    const long long cp = I.sstride;  // floats from one slot to the next
+    const long long cp = T.cp;  // floats from one slot to the next
     // this lane's pair at slot 0 (8-byte aligned: state_off, cp, r0 are even)
-    float* st = a.state + I.state_off + r0 + 2 * p;
+    float* st = a.state + T.state_off + r0 + 2 * p;
+        float* sto = st + (long long)off_own * cp;  // this lane's pair at the own segment
+    const int cpi = (int)cp;
+    // angles of the first warp step, in flight during the table fill
+    float2 vn = make_float2(0.0f, 0.0f);
+    {
+        const int j = warp * SPW + s;
+        if (has0 && j < n_own) vn = *reinterpret_cast<const float2*>(sto + j * cpi);
+    }
     const int spread = tile & (kSpread - 1);
 
     // -- table of the other colour, raw: entry 1 + e, pair p ----------------------
@@ -169,7 +178,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
 
     // -- own-colour constants of the tile (built once per batch) ---------------
     {
-        const long long b = I.slot_off + off_own;
+        const long long b = slot_off + off_own;
         constexpr uint32_t kRow = (uint32_t)CB * P;  // bytes per table entry
         for (int j = tid; j < n_own; j += NT) {
             const uint2 r = a.slot_ref[b + j];
@@ -197,7 +206,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     //    sample neighbours on energy passes ------------------------------------
     float2 esum = f2(0.0f);  // energies of the pair's two chains
     if (has0) {
-        const float4* fcs = a.slot_cs + I.slot_off + off_oth;
+        const float4* fcs = a.slot_cs + slot_off + off_oth;
         unsigned char* t = tab + (size_t)((1 + e_lo) * P + p) * CB;
         for (int e = e_lo; e < n_ent; e += NTP, t += (size_t)NTP * P * CB) {
             const float2 v = *reinterpret_cast<const float2*>(t);
@@ -220,7 +229,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
                 }
             } else if (energy && e < n_oth) {
                 // GMRF: bonds to the sample neighbours from the sample plane
-                const uint32_t pos = a.slot_pos[I.slot_off + off_oth + e];
+                const uint32_t pos = a.slot_pos[slot_off + off_oth + e];
                 const int X = (int)(pos & 0xFFFFu), Y = (int)(pos >> 16);
                 const float* sp = a.samp + I.site_off + (long long)Y * I.Lx + X;
                 float vs[4] = {Y > 0 ? sp[-I.Lx] : -1.0f, Y + 1 < I.Ly ? sp[I.Lx] : -1.0f,
@@ -242,15 +251,8 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     const float c_acc = 1.4426950408889634f * I.invT;  // log2(e) / T
     unsigned cnt0 = 0, cnt1 = 0;
     const int n_steps = (n_own + SPW - 1) / SPW;
-    float* sto = st + (long long)off_own * cp;  // this lane's pair at the own segment
-    const int cpi = (int)cp;
     const unsigned char* tabp = tab + p * CB;  // this lane's column of the table
     // angles of a warp step: loaded one step ahead, in flight during the step before
-    float2 vn = make_float2(0.0f, 0.0f);
-    {
-        const int j = warp * SPW + s;
-        if (has0 && j < n_own) vn = *reinterpret_cast<const float2*>(sto + j * cpi);
-    }
     for (int g = warp; g < n_steps; g += NW) {  // warp-uniform
         const float2 vc = vn;
         {
@@ -353,9 +355,9 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         // barrier.  Fire-and-forget adds: with one chain group per tile each
         // address gets one add per pass.
         const bool accum2 = (a.flags & kAccumulate2) != 0;
-        double* acc1 = a.acc1 + I.slot_off + off_own;
-        double* acc2 = a.acc2 + I.slot_off + off_own;
-        const float* base = a.state + I.state_off + (long long)off_own * cp + r0;
+        double* acc1 = a.acc1 + slot_off + off_own;
+        double* acc2 = a.acc2 + slot_off + off_own;
+        const float* base = a.state + T.state_off + (long long)off_own * cp + r0;
         const bool vec4 = ((cp | r0 | ng) & 3) == 0;  // 16-byte aligned runs of 4 chains
         for (int j = tid; j < n_own; j += NT) {
             const float* src = base + (long long)j * cp;
@@ -405,7 +407,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
 }
 
 template <int TX, int TY, int NW, int P, bool ACC, int MODEL>
-cudaError_t launch_one(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
+cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, bool setup_only) {
     using Cf = Cfg<TX, TY, NW, MODEL>;
     static_assert(Cf::smem_max <= 227 * 1024, "shared memory");
     static bool attr_set = false;
@@ -418,19 +420,19 @@ cudaError_t launch_one(const SweepArgs& a, int n_tiles, cudaStream_t s, bool set
     }
     if (setup_only) return cudaSuccess;
     if (a.gt < 1 || a.gt > Cf::GT) return cudaErrorInvalidValue;
-    dim3 grid(n_tiles, (a.chain_end - a.chain0 + a.chain_group - 1) / a.chain_group);
+    dim3 grid(a.n_list, (a.chain_end - a.chain0 + a.chain_group - 1) / a.chain_group);
     tiled_pass_kernel<TX, TY, NW, P, ACC, MODEL><<<grid, Cf::NT, Cf::smem_for(a.gt, P), s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TX, int TY, int NW, int P, int MODEL>
-cudaError_t launch_cfg(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
+cudaError_t launch_cfg(const SweepArgs& a, cudaStream_t s, bool setup_only) {
     if (setup_only) {
-        cudaError_t e = launch_one<TX, TY, NW, P, false, MODEL>(a, n_tiles, s, true);
-        return e != cudaSuccess ? e : launch_one<TX, TY, NW, P, true, MODEL>(a, n_tiles, s, true);
+        cudaError_t e = launch_one<TX, TY, NW, P, false, MODEL>(a, s, true);
+        return e != cudaSuccess ? e : launch_one<TX, TY, NW, P, true, MODEL>(a, s, true);
     }
-    if (a.flags & kAccumulate) return launch_one<TX, TY, NW, P, true, MODEL>(a, n_tiles, s, false);
-    return launch_one<TX, TY, NW, P, false, MODEL>(a, n_tiles, s, false);
+    if (a.flags & kAccumulate) return launch_one<TX, TY, NW, P, true, MODEL>(a, s, false);
+    return launch_one<TX, TY, NW, P, false, MODEL>(a, s, false);
 }
 
 // pairs per site for a chain group of cg chains: the next power of two of
@@ -443,13 +445,13 @@ inline int pairs_for_group(int cg) {
 }
 
 template <int TX, int TY, int NW, int MODEL>
-cudaError_t launch_shape(const SweepArgs& a, int n_tiles, cudaStream_t s, bool setup_only) {
+cudaError_t launch_shape(const SweepArgs& a, cudaStream_t s, bool setup_only) {
     switch (pairs_for_group(a.chain_group)) {
-        case 1: return launch_cfg<TX, TY, NW, 1, MODEL>(a, n_tiles, s, setup_only);
-        case 2: return launch_cfg<TX, TY, NW, 2, MODEL>(a, n_tiles, s, setup_only);
-        case 4: return launch_cfg<TX, TY, NW, 4, MODEL>(a, n_tiles, s, setup_only);
-        case 8: return launch_cfg<TX, TY, NW, 8, MODEL>(a, n_tiles, s, setup_only);
-        default: return launch_cfg<TX, TY, NW, 16, MODEL>(a, n_tiles, s, setup_only);
+        case 1: return launch_cfg<TX, TY, NW, 1, MODEL>(a, s, setup_only);
+        case 2: return launch_cfg<TX, TY, NW, 2, MODEL>(a, s, setup_only);
+        case 4: return launch_cfg<TX, TY, NW, 4, MODEL>(a, s, setup_only);
+        case 8: return launch_cfg<TX, TY, NW, 8, MODEL>(a, s, setup_only);
+        default: return launch_cfg<TX, TY, NW, 16, MODEL>(a, s, setup_only);
     }
 }
 

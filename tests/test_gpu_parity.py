@@ -212,13 +212,15 @@ def test_tiled_and_plain_paths_agree_bitwise():
 
 @pytest.mark.parametrize("tile", [(16, 16), (32, 16), (32, 32)])
 def test_tile_shapes_and_chain_groups_agree_bitwise(tile):
+    """9 realisations in chain groups of 4 (two groups and a launch of its own for the
+    ninth), of 8 (one group and the ninth) and of 9 (one group with a padded row)."""
     zs, gs = ragged_images()
-    R = 5
+    R = 9
     ref = make_ctx(zs, gs, R, "plain")
     ref.set_T([0.2, 0.2, 0.1, 0.4])
     ref.sweep(3, "equil")
     want = [s.cpu().numpy() for s in ref.get_state()]
-    for cg in (2, 4, 5):
+    for cg in (4, 8, 9):
         ctx = make_ctx(zs, gs, R, "tiled", tile=tile, chain_group=cg)
         ctx.set_T([0.2, 0.2, 0.1, 0.4])
         ctx.sweep(3, "equil")
