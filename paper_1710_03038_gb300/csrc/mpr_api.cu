@@ -46,7 +46,7 @@ constexpr double kPiD = 3.14159265358979323846;
 
 // Byte offsets of the workspace regions of one context.
 struct Layout {
-    size_t img, ctl, ch_a, ch_cnt, ch_last, ch_ecur, ch_elast, ch_esum, ch_esum2;
+    size_t img, ctl, ch_a, ch_alpha, ch_cnt, ch_last, ch_ecur, ch_elast, ch_esum, ch_esum2;
     size_t zst, gst, outst, eout, samp, slot_map, tiles, counts, halo, tile_list, scratch;
     size_t slot_pos, slot_ref, slot_cs, acc1, acc2, state, newton, hist, sub;
     size_t total;
@@ -110,6 +110,7 @@ Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_im
     L.img = take(sizeof(ImgDev) * g.n_img);
     L.ctl = take(sizeof(Control));
     L.ch_a = take(sizeof(float) * NC);
+    L.ch_alpha = take(sizeof(float) * NC);
     L.ch_cnt = take(sizeof(uint32_t) * NC * kSpread);
     L.ch_last = take(sizeof(uint32_t) * NC);
     L.ch_ecur = take(sizeof(double) * NC * kSpread);
@@ -224,6 +225,7 @@ void bind_views(mpr_ctx* c) {
     c->d_img = at<ImgDev>(w, L.img);
     c->d_ctl = at<Control>(w, L.ctl);
     c->ch.a = at<float>(w, L.ch_a);
+    c->ch.alpha = at<float>(w, L.ch_alpha);
     c->ch.acc_cnt = at<uint32_t>(w, L.ch_cnt);
     c->ch.acc_last = at<uint32_t>(w, L.ch_last);
     c->ch.e_cur = at<double>(w, L.ch_ecur);
@@ -396,6 +398,7 @@ __global__ void init_chains_kernel(ChainDev ch, int nc) {
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
         ch.a[i] = 1.0f;
+        ch.alpha[i] = proposal_width(1.0f);
         ch.acc_last[i] = 0;
         ch.e_last[i] = __longlong_as_double(0x7FF8000000000000LL);
         ch.e_sum[i] = 0.0;
@@ -404,6 +407,11 @@ __global__ void init_chains_kernel(ChainDev ch, int nc) {
 }
 
 // ======================================================= sweep kernels
+
+__global__ void set_alpha_kernel(ChainDev ch, int nc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) ch.alpha[i] = proposal_width(ch.a[i]);
+}
 
 // Bookkeeping after every sweep: acceptance -> a (Alg. 2 step 4.2), energy
 // record (step 4.3), counters.  One block; one warp per chain at a time sums
@@ -425,8 +433,10 @@ __global__ void end_sweep_kernel(const ImgDev* img, ChainDev ch, Control* ctl, i
         e_gap = warp_sum(e_gap);
         if (lane != 0) continue;
         ch.acc_last[c] = cnt;
-        if (equil && (double)cnt < A_targ * (double)I.n_gap)
+        if (equil && (double)cnt < A_targ * (double)I.n_gap) {
             ch.a[c] = (float)(1.0 + (double)(i + 1) / k_a);
+            ch.alpha[c] = proposal_width(ch.a[c]);
+        }
         if (record) {
             const double e = (e_gap + (add_ess ? I.E_ss : 0.0)) / I.n_bonds;
             ch.e_last[c] = e;
@@ -1690,6 +1700,8 @@ mpr_status mpr_set_chain_a(mpr_ctx* c, const float* a, mpr_stream stream) {
         if (!(a[i] >= 1.0f) || !std::isfinite(a[i])) return fail(MPR_ERR_INVALID_ARG, "a must be >= 1");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     MPR_CUDA(cudaMemcpyAsync(c->ch.a, a, sizeof(float) * nc, cudaMemcpyHostToDevice, s));
+    set_alpha_kernel<<<grid_for(nc), 256, 0, s>>>(c->ch, nc);
+    MPR_CUDA(cudaGetLastError());
     MPR_CUDA(cudaStreamSynchronize(s));
     return MPR_OK;
 }

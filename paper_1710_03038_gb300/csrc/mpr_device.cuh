@@ -126,14 +126,15 @@ __device__ __forceinline__ float2 sin_taylor2(float2 t) {
     return mul2(t, fma2(mul2(t2, f2(-1.0f)), p, f2(1.0f)));
 }
 
-// atan2(y, x) of both components for |x| + |y| > 0: octant reduction to
+// atan2(y, x) of both components (finite for x = y = 0): octant reduction to
 // t = min/max in [0, 1] and an odd degree-15 polynomial t P(t^2) for atan(t)
 // whose coefficients were fitted here (minimax in the absolute error on
 // [0, 1], 3.8e-8 in exact arithmetic; about 1.2e-7 rad in FP32 including the
 // approximate reciprocal).
 __device__ __forceinline__ float2 atan2_pair(float2 y, float2 x) {
     const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
-    const float2 mx = make_float2(fmaxf(ax0, ay0), fmaxf(ax1, ay1));
+    // the floor keeps t finite (0) for a vanishing field
+    const float2 mx = make_float2(fmaxf(fmaxf(ax0, ay0), 1e-30f), fmaxf(fmaxf(ax1, ay1), 1e-30f));
     const float2 mn = make_float2(fminf(ax0, ay0), fminf(ax1, ay1));
     const float2 t = mul2(mn, make_float2(rcp_approx(mx.x), rcp_approx(mx.y)));
     const float2 t2 = mul2(t, t);
@@ -168,6 +169,12 @@ struct UpdateConst {
 // words (0, 1) for the even realisation and (2, 3) for the odd one, as
 // u = (w >> 8) 2^-24.  The proposal uses (u - 1/2) alpha = (w >> 8 - 2^23)
 // (alpha 2^-24) (the same product, the power of two being exact).
+// (2 pi / a) 2^-24: the proposal half-range alpha = 2 pi / a of Alg. 1 step 3
+// in units of the 24-bit uniform (the power of two is exact)
+__host__ __device__ __forceinline__ float proposal_width(float a) {
+    return (6.28318530717958647692f / a) * 0x1p-24f;
+}
+
 struct PairRand {
     float2 um;  // (w >> 8) - 2^23 of both realisations (exact integers)
     float2 r;   // acceptance uniforms
@@ -198,9 +205,11 @@ __device__ __forceinline__ PairOut metropolis_pair(float2 phi1, float2 mPsi, flo
                                                    const PairRand& u, const UpdateConst& k,
                                                    float2 alpha_s, float c_acc) {
     float2 phi2 = fma2(alpha_s, u.um, phi1);
-    // mod 2 pi: phi2 lies in (-pi, 3 pi)
-    phi2 = sel2(phi2.x < 0.0f, phi2.y < 0.0f, add2(phi2, f2(kTwoPi)),
-                sel2(phi2.x >= kTwoPi, phi2.y >= kTwoPi, add2(phi2, f2(-kTwoPi)), phi2));
+    // mod 2 pi for phi2 in (-pi, 3 pi): phi2 - 2 pi floor(phi2 / 2 pi) gives the
+    // same bits as adding or subtracting 2 pi below 0 or from 2 pi up (checked
+    // for every FP32 value of the range; they differ only at -0 and negative
+    // denormals, which this update cannot produce)
+    phi2 = fma2(f2(-kTwoPi), floor2(mul2(phi2, f2(kInvTwoPi))), phi2);
     const float2 x = fma2(f2(k.q), phi1, mPsi);
     const float2 h = mul2(f2(0.5f * k.q), rsub2(phi1, phi2));
     // x + h lies in (-3 pi/2, 5 pi/2): the hardware sine reduces that range itself
@@ -233,9 +242,10 @@ __device__ __forceinline__ PairOut hybrid_pair(float2 phi, float2 C, float2 S, c
                                                const UpdateConst& k, float2 alpha_s, float c_acc) {
     const float2 R2 = fma2(C, C, mul2(S, S));
     const bool f0 = R2.x > kFieldEps2, f1 = R2.y > kFieldEps2;
-    const float2 Psi = sel2(f0, f1, atan2_pair(S, C), f2(0.0f));
-    const float2 R = sel2(f0, f1, mul2(R2, make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y))),
-                          f2(0.0f));
+    // a field below 1e-12 gives R ~ 0 (no energy change) and no reflection below
+    const float2 Psi = atan2_pair(S, C);
+    const float2 R = mul2(R2, make_float2(rsqrt_approx(fmaxf(R2.x, 1e-30f)),
+                                          rsqrt_approx(fmaxf(R2.y, 1e-30f))));
     float2 t = fma2(f2(2.0f), Psi, mul2(f2(-k.q), phi));
     t = fma2(f2(-kTwoPi), floor2(mul2(t, f2(kInvTwoPi))), t);
     const float2 ref = mul2(t, f2(k.inv_q));
@@ -280,8 +290,7 @@ __device__ __forceinline__ PairOut gmrf_pair(float2 phi, float2 sum, float n, co
     const float2 t = fma2(f2(2.0f), m, mul2(f2(-1.0f), phi));
     const float2 phi1 = sel2(t.x >= 0.0f && t.x < kTwoPi, t.y >= 0.0f && t.y < kTwoPi, t, phi);
     float2 phi2 = fma2(alpha_s, u.um, phi1);
-    phi2 = sel2(phi2.x < 0.0f, phi2.y < 0.0f, add2(phi2, f2(kTwoPi)),
-                sel2(phi2.x >= kTwoPi, phi2.y >= kTwoPi, add2(phi2, f2(-kTwoPi)), phi2));
+    phi2 = fma2(f2(-kTwoPi), floor2(mul2(phi2, f2(kInvTwoPi))), phi2);  // mod 2 pi
     constexpr float kInvTwoPi2 = 0.050660591821168885f;  // 1 / (2 pi^2)
     const float2 d = rsub2(phi1, phi2);
     const float2 s = fma2(f2(-2.0f), m, add2(phi2, phi1));

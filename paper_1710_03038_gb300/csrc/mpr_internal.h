@@ -61,6 +61,7 @@ constexpr int kSpread = 32;
 // e_cur are kSpread times longer).
 struct ChainDev {
     float* a;
+    float* alpha;         // (2 pi / a) 2^-24: the proposal width in units of the 24-bit uniform
     uint32_t* acc_cnt;    // accepted proposals of the sweep in progress
     uint32_t* acc_last;   // of the last completed sweep
     double* e_cur;        // bond energy (gap-related part) reduced during the sweep

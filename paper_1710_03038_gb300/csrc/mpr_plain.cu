@@ -56,9 +56,10 @@ plain_pass_kernel(SweepArgs a) {
         float2 phi_now = make_float2(angle_of(v0), angle_of(P1[i]));
         if (!is_fixed(v0)) {
             const int cg = img * a.n_chains + ch0;
-            const float a0 = (a.flags & kAlphaOne) ? 1.0f : a.ch.a[cg];
-            const float a1 = ((a.flags & kAlphaOne) || !has1) ? 1.0f : a.ch.a[cg + 1];
-            const float2 alpha_s = mul2(make_float2(kTwoPi / a0, kTwoPi / a1), f2(0x1p-24f));
+            const float2 alpha_s =
+                (a.flags & kAlphaOne)
+                    ? f2(proposal_width(1.0f))
+                    : make_float2(a.ch.alpha[cg], has1 ? a.ch.alpha[cg + 1] : 0.0f);
             const float c_acc = 1.4426950408889634f * I.invT;
             const uint4 w = philox4x32_10(
                 site_counter(x, y, colour, sweep, (uint32_t)ch0, (uint32_t)img | a.img_tag), a.key);

@@ -244,10 +244,10 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
 
     // -- own colour: every site of every chain of the group ---------------------
     const int ch0 = t_img * a.n_chains + r0 + 2 * p;
-    const float a0 = ((a.flags & kAlphaOne) || !has0) ? 1.0f : a.ch.a[ch0];
-    const float a1 = ((a.flags & kAlphaOne) || !has1) ? 1.0f : a.ch.a[ch0 + 1];
-    // alpha 2^-24 = (2 pi / a) 2^-24 per chain (the power of two is exact)
-    const float2 alpha_s = mul2(make_float2(kTwoPi / a0, kTwoPi / a1), f2(0x1p-24f));
+    const float2 alpha_s =
+        (a.flags & kAlphaOne)
+            ? f2(proposal_width(1.0f))
+            : make_float2(has0 ? a.ch.alpha[ch0] : 0.0f, has1 ? a.ch.alpha[ch0 + 1] : 0.0f);
     const float c_acc = 1.4426950408889634f * I.invT;  // log2(e) / T
     unsigned cnt0 = 0, cnt1 = 0;
     const int n_steps = (n_own + SPW - 1) / SPW;
