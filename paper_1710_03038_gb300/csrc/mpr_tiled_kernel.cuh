@@ -336,42 +336,33 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         if (energy) esum = add2(esum, make_float2(act ? o.e.x : 0.0f, act1 ? o.e.y : 0.0f));
     }
 
-    // -- per-chain totals: lanes of one pair, then warps ------------------------
-    float e0 = esum.x, e1 = esum.y;
-#pragma unroll
-    for (int o = P; o < 32; o <<= 1) {
-        cnt0 += __shfl_xor_sync(0xffffffffu, cnt0, o);
-        cnt1 += __shfl_xor_sync(0xffffffffu, cnt1, o);
-        if (energy) {
-            e0 += __shfl_xor_sync(0xffffffffu, e0, o);
-            e1 += __shfl_xor_sync(0xffffffffu, e1, o);
-        }
-    }
-    if (lane < P) red[warp * P + lane] = make_float4(e0, e1, __uint_as_float(cnt0), __uint_as_float(cnt1));
-    __syncthreads();
     if (ACC) {
-        // realisation sums: the block's new angles are read back (from L2, past
-        // L1) one site per thread; the stores of the block are visible after the
-        // barrier.  Fire-and-forget adds: with one chain group per tile each
-        // address gets one add per pass.
+        // realisation sums of the sites this warp updated: their rows are read
+        // back (from L2, past L1) one site per lane, ordered after the warp's
+        // stores by the warp barrier, and added to the FP64 sums with
+        // fire-and-forget adds (one chain group per tile: one add per address)
+        __syncwarp();
         const bool accum2 = (a.flags & kAccumulate2) != 0;
         double* acc1 = a.acc1 + slot_off + off_own;
         double* acc2 = a.acc2 + slot_off + off_own;
         const float* base = a.state + T.state_off + (long long)off_own * cp + r0;
         const bool vec4 = ((cp | r0 | ng) & 3) == 0;  // 16-byte aligned runs of 4 chains
-        for (int j = tid; j < n_own; j += NT) {
+        const int n_mine = warp < n_steps ? ((n_steps - 1 - warp) / NW + 1) * SPW : 0;
+        for (int k = lane; k < n_mine; k += 32) {
+            const int j = (warp + (k / SPW) * NW) * SPW + (k % SPW);
+            if (j >= n_own) continue;
             const float* src = base + (long long)j * cp;
             float2 s1 = f2(0.0f), s2 = f2(0.0f);
             if (vec4) {
-                for (int k = 0; k < ng; k += 4) {
-                    const float4 v = __ldcg(reinterpret_cast<const float4*>(src + k));
+                for (int q = 0; q < ng; q += 4) {
+                    const float4 v = __ldcg(reinterpret_cast<const float4*>(src + q));
                     const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
                     s1 = add2(s1, add2(lo, hi));
                     s2 = fma2(lo, lo, fma2(hi, hi, s2));
                 }
             } else {
-                for (int k = 0; k + 1 < ng; k += 2) {
-                    const float2 v = __ldcg(reinterpret_cast<const float2*>(src + k));
+                for (int q = 0; q + 1 < ng; q += 2) {
+                    const float2 v = __ldcg(reinterpret_cast<const float2*>(src + q));
                     s1 = add2(s1, v);
                     s2 = fma2(v, v, s2);
                 }
@@ -385,6 +376,20 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
             if (accum2) atomicAdd(acc2 + j, (double)(s2.x + s2.y));
         }
     }
+
+    // -- per-chain totals: lanes of one pair, then warps ------------------------
+    float e0 = esum.x, e1 = esum.y;
+#pragma unroll
+    for (int o = P; o < 32; o <<= 1) {
+        cnt0 += __shfl_xor_sync(0xffffffffu, cnt0, o);
+        cnt1 += __shfl_xor_sync(0xffffffffu, cnt1, o);
+        if (energy) {
+            e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+            e1 += __shfl_xor_sync(0xffffffffu, e1, o);
+        }
+    }
+    if (lane < P) red[warp * P + lane] = make_float4(e0, e1, __uint_as_float(cnt0), __uint_as_float(cnt1));
+    __syncthreads();
     if (tid < P && 2 * tid < ng) {
         double E0 = 0.0, E1 = 0.0;
         unsigned n0 = 0, n1 = 0;
