@@ -34,7 +34,7 @@
 
 #define OR_PI 3.14159265358979323846
 #define OR_TWO_PI 6.28318530717958647692
-#define OR_EPS_FIELD 1e-12
+#define OR_EPS_FIELD 1e-6  /* a local field shorter than this vanishes (no reflection) */
 
 /* ---------------------------------------------------------------- Philox */
 
@@ -196,7 +196,11 @@ static int neighbours(int Lx, int Ly, int x, int y, long nb[4])
  * phi' = (2 Phi - phi) mod 2pi with Phi = atan2(sum sin phi_j, sum cos phi_j).
  * `slack` (nullable) receives the distance of the reflected angle to the
  * nearest point where the result jumps (a multiple of 2 pi before the modulo,
- * or 2 pi q after it); `field` (nullable) receives the local-field length. */
+ * or 2 pi q after it); `field` (nullable) receives the local-field length.
+ * atan2 needs a field of nonzero length; one shorter than 1e-6 (a few units
+ * of the resolution of a sum of four unit vectors in single precision, and
+ * the exact value 0 of antipodal neighbours, e.g. the sample extremes 0 and
+ * 2 pi at q = 1/2) counts as vanishing and leaves the spin unreflected. */
 double oracle_over_relax(double phi, const double* nbr, int n, double q, int literal,
                          double* slack, double* field)
 {
@@ -208,7 +212,8 @@ double oracle_over_relax(double phi, const double* nbr, int n, double q, int lit
     }
     double R = sqrt(C * C + S * S);
     if (field) *field = R;
-    if (R < OR_EPS_FIELD) { if (slack) *slack = 0.0; return phi; }
+    /* no reflection is attempted: no range decision to report (the field test is) */
+    if (R < OR_EPS_FIELD) { if (slack) *slack = 1e30; return phi; }
     double Psi = atan2(S, C);
     if (literal) {
         double t = 2.0 * Psi - phi;

@@ -11,7 +11,7 @@ namespace mpr {
 constexpr float kTwoPi = 6.28318530717958647692f;    // rounds up: 6.2831855f
 constexpr float kInvTwoPi = 0.15915494309189533577f;
 constexpr float kPi = 3.14159265358979323846f;
-constexpr float kFieldEps2 = 1e-24f;                   // |field| < 1e-12: no reflection
+constexpr float kFieldEps2 = 1e-12f;                   // |field| < 1e-6: vanishing field
 
 // --------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 -> 64-bit
@@ -235,17 +235,18 @@ __device__ __forceinline__ PairOut metropolis_pair(float2 phi1, float2 mPsi, flo
 // with angles phi and neighbour fields (C, S) = sum_j (cos q phi_j, sin q phi_j):
 // over-relaxation (Eq. over-relax, q-consistent): Psi = atan2(S, C),
 // theta' = (2 Psi - q phi) mod 2 pi, phi' = theta'/q if theta' < 2 pi q (else
-// phi' = phi; no reflection when |field| < 1e-12); then the restricted
+// phi' = phi; a field shorter than 1e-6 vanishes: no reflection and no energy
+// change); then the restricted
 // Metropolis step.
 template <bool ENERGY>
 __device__ __forceinline__ PairOut hybrid_pair(float2 phi, float2 C, float2 S, const PairRand& u,
                                                const UpdateConst& k, float2 alpha_s, float c_acc) {
     const float2 R2 = fma2(C, C, mul2(S, S));
     const bool f0 = R2.x > kFieldEps2, f1 = R2.y > kFieldEps2;
-    // a field below 1e-12 gives R ~ 0 (no energy change) and no reflection below
-    const float2 Psi = atan2_pair(S, C);
-    const float2 R = mul2(R2, make_float2(rsqrt_approx(fmaxf(R2.x, 1e-30f)),
-                                          rsqrt_approx(fmaxf(R2.y, 1e-30f))));
+    const float2 Psi = atan2_pair(S, C);  // finite for any field; unused when it vanishes
+    const float2 R = sel2(f0, f1, mul2(R2, make_float2(rsqrt_approx(fmaxf(R2.x, 1e-30f)),
+                                                       rsqrt_approx(fmaxf(R2.y, 1e-30f)))),
+                          f2(0.0f));
     float2 t = fma2(f2(2.0f), Psi, mul2(f2(-k.q), phi));
     t = fma2(f2(-kTwoPi), floor2(mul2(t, f2(kInvTwoPi))), t);
     const float2 ref = mul2(t, f2(k.inv_q));

@@ -226,9 +226,18 @@ def test_printed_q1_formula_does_not_conserve_q_half_energy():
 
 
 def test_over_relaxation_zero_field():
-    """atan2 needs |x| + |y| > 0: with a vanishing field the spin is left alone."""
+    """atan2 needs |x| + |y| > 0: with a vanishing field the spin is left alone.  The
+    sample extremes 0 and 2 pi are antipodal at q = 1/2 (their field is exactly 0);
+    fields shorter than 1e-6 count as vanishing, longer ones reflect."""
     p1, _, field = oracle.over_relax(1.0, np.array([0.0, TWO_PI]), q=0.5)
     assert field < 1e-12 and p1 == 1.0
+    p1, _, field = oracle.over_relax(1.0, np.array([0.0, TWO_PI - 1e-7]), q=0.5)
+    assert 1e-9 < field < 1e-6 and p1 == 1.0
+    p1, _, field = oracle.over_relax(1.0, np.array([0.0, TWO_PI - 1e-4]), q=0.5)
+    assert field > 1e-6 and p1 != 1.0
+    # the reflection at that field conserves the site energy as everywhere else
+    assert abs(_site_energy(p1, np.array([0.0, TWO_PI - 1e-4]), 0.5)
+               - _site_energy(1.0, np.array([0.0, TWO_PI - 1e-4]), 0.5)) < 1e-12
 
 
 # -------------------------------------------------- Metropolis limits, Alg. 1
