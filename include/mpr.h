@@ -80,14 +80,14 @@ typedef struct {
     int path;                /* mpr_path                                                       */
     int tile_x, tile_y;      /* tiled path tile shape (16x16, 32x16 or 32x32); 0 = 16x16
                                 (mpr_autotune times all three)                                 */
-    int chain_group;         /* tiled path: chains per thread block, even or >= n_chains;
-                                values above 32 act as 32; 0 = automatic                       */
+    int chain_group;         /* tiled path: chains per thread block, a multiple of 4 or
+                                >= n_chains; values above 32 act as 32; 0 = automatic          */
     int literal_or;          /* 1: over-relaxation as printed in Eq. over-relax (q = 1 field,
-                                always applied), for comparison; plain path only; 0           */
+                                always applied), for comparison; tiled path: 16x16 tiles; 0    */
     int use_graphs;          /* 1: runs of 4 or more sweeps on a non-default stream are captured
                                 once into a CUDA graph and replayed; 1                         */
-    int model;               /* mpr_model; MPR_MODEL_GMRF runs on the plain path (its
-                                over-relaxation reflects about the neighbour mean); MPR        */
+    int model;               /* mpr_model (MPR_MODEL_GMRF: the over-relaxation reflects about
+                                the neighbour mean; tiled path: 16x16 tiles); MPR              */
 } mpr_params;
 
 /* Options of the specific-energy-matching temperature estimate (Sec. 2.3). */
@@ -237,6 +237,19 @@ mpr_status mpr_predict(mpr_ctx* ctx, float* z_hat, float* z_std, mpr_mem where,
 /* Clears the realisation accumulators (keeps the chains' states). */
 mpr_status mpr_reset_accumulators(mpr_ctx* ctx, mpr_stream stream);
 
+/* The realisation sums behind mpr_predict (Alg. 2 step 5): for every gap
+ * pixel the sum, over every chain and every measurement sweep so far, of phi
+ * and of phi^2; 0 at sample pixels.  sum, sum2 (nullable): [sum Lx*Ly]
+ * doubles, image-major, row-major, on the host (blocking) or the device
+ * (asynchronous).  n_terms (host, nullable) receives the number of terms of
+ * each sum (measurement sweeps x chains).  mpr_set_accumulators restores
+ * them, e.g. to resume a checkpointed sampling run (sum2 may be NULL: the
+ * squares restart at 0); n_terms must be a multiple of the chain count. */
+mpr_status mpr_get_accumulators(mpr_ctx* ctx, double* sum, double* sum2, int64_t* n_terms,
+                                mpr_mem where, mpr_stream stream);
+mpr_status mpr_set_accumulators(mpr_ctx* ctx, const double* sum, const double* sum2,
+                                int64_t n_terms, mpr_mem where, mpr_stream stream);
+
 /* Checkpoint / parity access to the full simulation state.
  * phi: [sum over images of n_chains * Lx * Ly] floats, image-major then
  * chain-major, row-major; get writes sample pixels with their fixed angles,
@@ -270,12 +283,22 @@ void mpr_destroy(mpr_ctx* ctx);
 mpr_status mpr_lattice_energy(int n, const int* Lx, const int* Ly, const float* phi,
                               double q, double J, double* H_out, mpr_stream stream);
 
-/* Gradient of the same energy: grad_i = g_k * J q sum_j sin(q (phi_i - phi_j))
- * for site i of grid k, with g device [n] FP64 upstream weights (dL/dH_k).
- * grad device, same layout as phi.  (dH/dJ = H/J needs no kernel.) */
+/* Gradient of the same energy with respect to the angles: grad_i = g_k * J q
+ * sum_j sin(q (phi_i - phi_j)) for site i of grid k (the torque, the local
+ * field of the sweep), with g device [n] FP64 upstream weights (dL/dH_k).
+ * grad device, same layout as phi.  Asynchronous. */
 mpr_status mpr_lattice_torque(int n, const int* Lx, const int* Ly, const float* phi,
                               double q, double J, const double* g, float* grad,
                               mpr_stream stream);
+
+/* Both gradients of L = sum_k g_k H_k in one pass (the backward of the energy
+ * as a differentiable function of the angles and of J): grad_phi as
+ * mpr_lattice_torque (nullable), and grad_J device [1] FP64 (nullable)
+ * = sum_k g_k dH_k/dJ = -sum_k g_k sum_<ij> cos(q (phi_i - phi_j)) (= H/J,
+ * Eq. Hamiltonian_mod being linear in J).  Asynchronous. */
+mpr_status mpr_lattice_grad(int n, const int* Lx, const int* Ly, const float* phi, double q,
+                            double J, const double* g, float* grad_phi, double* grad_J,
+                            mpr_stream stream);
 
 /* Philox4x32-10 blocks of the library's random stream for n counters
  * (device uint32 [4n] in, [4n] out; key host [2]).  reference != 0 runs the

@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import MprParams, MprTOpts, call, int_array, i64_array
 
 __all__ = ["Params", "TOpts", "Context", "fill", "MPREnergy", "lattice_energy", "lattice_torque",
-           "philox", "version", "workspace_size"]
+           "lattice_grad", "philox", "version", "workspace_size"]
 
 
 def version() -> str:
@@ -40,10 +40,10 @@ class Params:
     freeze_a_in_measure: bool = True
     path: str = "tiled"          # "tiled" (batched) or "plain"
     tile: tuple = (0, 0)         # (tile_x, tile_y); (0, 0) = 16x16
-    chain_group: int = 0         # chains per thread block; 0 = automatic
-    literal_or: bool = False     # printed q = 1 over-relaxation (plain path, comparison only)
+    chain_group: int = 0         # chains per thread block (multiple of 4); 0 = automatic
+    literal_or: bool = False     # printed q = 1 over-relaxation (comparison only)
     use_graphs: bool = True      # replay captured CUDA graphs of sweep runs (non-default streams)
-    model: str = "mpr"           # "mpr" or "gmrf" (Sec. 4.3 pair interaction, plain path)
+    model: str = "mpr"           # "mpr" or "gmrf" (Sec. 4.3 pair interaction)
 
     def c(self) -> MprParams:
         p = MprParams()
@@ -265,6 +265,28 @@ class Context:
     def reset_accumulators(self, stream=None):
         call("mpr_reset_accumulators", self._ctx, _stream_ptr(stream))
 
+    def accumulators(self, stream=None):
+        """Realisation sums of phi and phi^2 per gap pixel (lists per image of [Ly, Lx]
+        float64 device tensors, 0 at samples) and their number of terms."""
+        s1 = torch.empty(self.n_sites, dtype=torch.float64, device=self.device)
+        s2 = torch.empty(self.n_sites, dtype=torch.float64, device=self.device)
+        n = C.c_int64()
+        call("mpr_get_accumulators", self._ctx, _ptr(s1), _ptr(s2), C.byref(n), _lib.MPR_DEVICE,
+             _stream_ptr(stream))
+        return self._split(s1), self._split(s2), n.value
+
+    def set_accumulators(self, sums, sums2, n_terms: int, stream=None):
+        """Restore realisation sums (as returned by accumulators()); sums2 may be None."""
+        s1 = torch.cat([torch.as_tensor(t, dtype=torch.float64, device=self.device).reshape(-1)
+                        for t in _as_list(sums)]).contiguous()
+        s2 = None
+        if sums2 is not None:
+            s2 = torch.cat([torch.as_tensor(t, dtype=torch.float64, device=self.device).reshape(-1)
+                            for t in _as_list(sums2)]).contiguous()
+        call("mpr_set_accumulators", self._ctx, _ptr(s1), _ptr(s2) if s2 is not None else None,
+             C.c_int64(int(n_terms)), _lib.MPR_DEVICE, _stream_ptr(stream))
+        self._keep = (s1, s2)
+
     def _split(self, flat):
         out, off = [], 0
         for (h, w) in self.shapes:
@@ -398,32 +420,50 @@ def lattice_torque(phi: torch.Tensor, g: torch.Tensor, q: float = 0.5, J: float 
     return grad
 
 
+def lattice_grad(phi: torch.Tensor, g: torch.Tensor, q: float = 0.5, J: float = 1.0,
+                 want_phi: bool = True, want_J: bool = True, stream=None):
+    """Both gradients of L = sum_k g_k H_k for a [..., Ly, Lx] float32 CUDA tensor:
+    (dL/dphi or None, dL/dJ as a float64 [1] device tensor or None), from one kernel."""
+    Ly, Lx = phi.shape[-2:]
+    n = int(np.prod(phi.shape[:-2])) if phi.dim() > 2 else 1
+    p = phi.contiguous()
+    gg = g.reshape(-1).to(torch.float64).contiguous()
+    gp = torch.empty_like(p) if want_phi else None
+    gJ = torch.empty(1, dtype=torch.float64, device=phi.device) if want_J else None
+    call("mpr_lattice_grad", n, int_array([Lx] * n), int_array([Ly] * n), _ptr(p), float(q),
+         float(J), _ptr(gg), _ptr(gp) if gp is not None else None,
+         _ptr(gJ) if gJ is not None else None, _stream_ptr(stream))
+    return gp, gJ
+
+
 class MPREnergy(torch.autograd.Function):
     """H(phi, J) = -J sum_<ij> cos(q (phi_i - phi_j)) with a hand-written backward.
 
-    forward returns H per grid (FP64); backward returns the torque
-    dH/dphi_i = J q sum_j sin(q (phi_i - phi_j)) times the upstream gradient,
-    and dH/dJ = H / J.
+    forward returns H per grid (FP64); backward returns, from the library's
+    gradient kernel, the torque dH/dphi_i = J q sum_j sin(q (phi_i - phi_j))
+    and dH/dJ = -sum_<ij> cos(q (phi_i - phi_j)), each weighted by the
+    upstream gradient.
     """
 
     @staticmethod
     def forward(ctx, phi, J, q=0.5):
         Jv = float(J.item()) if isinstance(J, torch.Tensor) else float(J)
         H = lattice_energy(phi, q=q, J=Jv)
-        ctx.save_for_backward(phi, H)
+        ctx.save_for_backward(phi)
         ctx.q = q
         ctx.J = Jv
-        ctx.J_is_tensor = isinstance(J, torch.Tensor)
-        ctx.J_device = J.device if ctx.J_is_tensor else None
+        ctx.J_tensor = J if isinstance(J, torch.Tensor) else None
         return H
 
     @staticmethod
     def backward(ctx, gH):
-        phi, H = ctx.saved_tensors
-        g_phi = lattice_torque(phi, gH.to(torch.float64), q=ctx.q, J=ctx.J)
-        g_J = None
-        if ctx.J_is_tensor:
-            g_J = (gH.to(torch.float64) * H / ctx.J).sum().to(ctx.J_device)
+        (phi,) = ctx.saved_tensors
+        want_J = ctx.J_tensor is not None and ctx.needs_input_grad[1]
+        g_phi, g_J = lattice_grad(phi, gH.to(torch.float64), q=ctx.q, J=ctx.J,
+                                  want_phi=ctx.needs_input_grad[0], want_J=want_J)
+        if g_J is not None:
+            J = ctx.J_tensor
+            g_J = g_J.reshape(J.shape).to(device=J.device, dtype=J.dtype)
         return g_phi, g_J, None
 
 

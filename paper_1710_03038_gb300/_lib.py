@@ -31,8 +31,10 @@ EXPORTS = (
     "mpr_estimate_T", "mpr_set_T", "mpr_get_T", "mpr_sweep", "mpr_energy", "mpr_predict",
     "mpr_reset_accumulators", "mpr_get_state", "mpr_set_state", "mpr_get_chain_info",
     "mpr_set_chain_a", "mpr_get_sweep_index", "mpr_set_sweep_index", "mpr_destroy",
-    "mpr_lattice_energy", "mpr_lattice_torque", "mpr_philox", "mpr_math_probe",
+    "mpr_lattice_energy", "mpr_lattice_torque", "mpr_lattice_grad", "mpr_philox",
+    "mpr_math_probe",
     "mpr_sample_energy_noalloc", "mpr_equilibrate", "mpr_get_energy_history",
+    "mpr_get_accumulators", "mpr_set_accumulators",
     "mpr_eT_table_workspace_size", "mpr_eT_table", "mpr_set_T_from_table", "mpr_autotune",
 )
 
@@ -94,6 +96,8 @@ def load(path: str = LIB_PATH):
             "mpr_energy": (i, [vp, vp, i, vp]),
             "mpr_predict": (i, [vp, vp, vp, i, vp]),
             "mpr_reset_accumulators": (i, [vp, vp]),
+            "mpr_get_accumulators": (i, [vp, vp, vp, i64p, i, vp]),
+            "mpr_set_accumulators": (i, [vp, vp, vp, C.c_int64, i, vp]),
             "mpr_get_state": (i, [vp, vp, i, vp]),
             "mpr_set_state": (i, [vp, vp, i, vp]),
             "mpr_get_chain_info": (i, [vp, fp, u32p, dp, vp]),
@@ -103,6 +107,7 @@ def load(path: str = LIB_PATH):
             "mpr_destroy": (None, [vp]),
             "mpr_lattice_energy": (i, [i, ip, ip, vp, d, d, vp, vp]),
             "mpr_lattice_torque": (i, [i, ip, ip, vp, d, d, vp, vp, vp]),
+            "mpr_lattice_grad": (i, [i, ip, ip, vp, d, d, vp, vp, vp, vp]),
             "mpr_philox": (i, [i, vp, u32p, vp, i, vp]),
             "mpr_math_probe": (i, [i, i, vp, vp, vp, vp]),
             "mpr_equilibrate": (i, [vp, i, i, i, ip, vp]),

@@ -602,6 +602,22 @@ __global__ void predict_kernel(const ImgDev* img, const double* acc1, const doub
     }
 }
 
+// Realisation sums <-> dense per-pixel arrays (dir 0: get, 1: set gap pixels).
+__global__ void acc_dense_kernel(const ImgDev* img, double* acc, const int* slot_map,
+                                 const float* samp, int tiled, double* dense, int dir) {
+    const ImgDev& I = img[blockIdx.y];
+    const long long n = (long long)I.Lx * I.Ly;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = I.site_off + i;
+        long long slot = -1;
+        if (tiled) slot = slot_map[s];
+        else if (samp[s] < 0.0f) slot = i;
+        if (dir == 0) dense[s] = slot < 0 ? 0.0 : acc[I.slot_off + slot];
+        else if (slot >= 0) acc[I.slot_off + slot] = dense[s];
+    }
+}
+
 // Chain-mean specific energy of every image after sweep i, into its ring.
 __global__ void sg_record_kernel(const ChainDev ch, double* hist, int n_img, int n_chains,
                                  uint32_t i) {
@@ -1639,6 +1655,52 @@ mpr_status mpr_reset_accumulators(mpr_ctx* c, mpr_stream stream) {
     MPR_CUDA(cudaMemsetAsync(c->d_acc1, 0, sizeof(double) * c->L.n_slots, s));
     MPR_CUDA(cudaMemsetAsync(c->d_acc2, 0, sizeof(double) * c->L.n_slots, s));
     c->n_meas_done = 0;
+    return MPR_OK;
+}
+
+// One accumulator array <-> a dense [sum Lx*Ly] double array (host buffers
+// go through the output staging area, 8 bytes per pixel).
+static mpr_status acc_copy(mpr_ctx* c, double* acc, double* dense, mpr_mem where, int dir,
+                           cudaStream_t s) {
+    const size_t N = (size_t)c->g.n_sites;
+    double* d = where == MPR_DEVICE ? dense : reinterpret_cast<double*>(c->d_out);
+    if (where == MPR_HOST && dir == 1)
+        MPR_CUDA(cudaMemcpyAsync(d, dense, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    long long maxn = 0;
+    for (int i = 0; i < c->g.n_img; ++i) maxn = std::max(maxn, (long long)c->g.Lx[i] * c->g.Ly[i]);
+    acc_dense_kernel<<<dim3(grid_for(maxn, 256, 1024), c->g.n_img), 256, 0, s>>>(
+        c->d_img, acc, c->d_slot_map, c->d_samp, c->g.path == MPR_PATH_TILED ? 1 : 0, d, dir);
+    MPR_CUDA(cudaGetLastError());
+    if (where == MPR_HOST) {
+        if (dir == 0) MPR_CUDA(cudaMemcpyAsync(dense, d, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaStreamSynchronize(s));
+    }
+    return MPR_OK;
+}
+
+mpr_status mpr_get_accumulators(mpr_ctx* c, double* sum, double* sum2, int64_t* n_terms,
+                                mpr_mem where, mpr_stream stream) {
+    if (!c) return fail(MPR_ERR_INVALID_ARG, "ctx is NULL");
+    if (where != MPR_HOST && where != MPR_DEVICE) return fail(MPR_ERR_INVALID_ARG, "bad mpr_mem");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (sum) MPR_TRY(acc_copy(c, c->d_acc1, sum, where, 0, s));
+    if (sum2) MPR_TRY(acc_copy(c, c->d_acc2, sum2, where, 0, s));
+    if (n_terms) *n_terms = (int64_t)c->n_meas_done * c->g.n_chains;
+    return MPR_OK;
+}
+
+mpr_status mpr_set_accumulators(mpr_ctx* c, const double* sum, const double* sum2,
+                                int64_t n_terms, mpr_mem where, mpr_stream stream) {
+    if (!c || !sum) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    if (where != MPR_HOST && where != MPR_DEVICE) return fail(MPR_ERR_INVALID_ARG, "bad mpr_mem");
+    if (n_terms < 0 || n_terms % c->g.n_chains != 0)
+        return fail(MPR_ERR_INVALID_ARG, "n_terms must be a multiple of the chain count");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    MPR_CUDA(cudaMemsetAsync(c->d_acc1, 0, sizeof(double) * c->L.n_slots, s));
+    MPR_CUDA(cudaMemsetAsync(c->d_acc2, 0, sizeof(double) * c->L.n_slots, s));
+    MPR_TRY(acc_copy(c, c->d_acc1, const_cast<double*>(sum), where, 1, s));
+    if (sum2) MPR_TRY(acc_copy(c, c->d_acc2, const_cast<double*>(sum2), where, 1, s));
+    c->n_meas_done = n_terms / c->g.n_chains;
     return MPR_OK;
 }
 

@@ -67,6 +67,43 @@ __global__ void lattice_torque_kernel(const __grid_constant__ Grids G, int k0, c
     }
 }
 
+// Both gradients of L = sum_k g_k H_k: the torque of every site (when grad is
+// non-null) and dL/dJ = -sum_k g_k sum over the right and down bonds of
+// cos(q dphi) (when gJ is non-null; FP32 bond terms, FP64 sums).
+__global__ void lattice_grad_kernel(const __grid_constant__ Grids G, int k0, const float* phi,
+                                    float q, float J, const double* up, float* grad,
+                                    double* gJ) {
+    const GridTable g = G.g[blockIdx.y];
+    const long long n = (long long)g.Lx * g.Ly;
+    const float* p = phi + g.off;
+    const double uk = up[k0 + blockIdx.y];
+    const float w = (float)uk * J * q;
+    double sJ = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.Lx), y = (int)(i / g.Lx);
+        const float v = p[i];
+        if (grad) {
+            float s = 0.0f;
+            if (y > 0) s += sinf(q * (v - p[i - g.Lx]));
+            if (y + 1 < g.Ly) s += sinf(q * (v - p[i + g.Lx]));
+            if (x > 0) s += sinf(q * (v - p[i - 1]));
+            if (x + 1 < g.Lx) s += sinf(q * (v - p[i + 1]));
+            grad[g.off + i] = w * s;
+        }
+        if (gJ) {
+            float e = 0.0f;
+            if (x + 1 < g.Lx) e -= cosf(q * (v - p[i + 1]));
+            if (y + 1 < g.Ly) e -= cosf(q * (v - p[i + g.Lx]));
+            sJ += (double)e;
+        }
+    }
+    if (gJ) {
+        sJ = warp_sum(sJ) * uk;
+        if ((threadIdx.x & 31) == 0 && sJ != 0.0) atomicAdd(gJ, sJ);
+    }
+}
+
 __global__ void philox_kernel(int n, const uint32_t* ctr, uint2 key, uint32_t* out, int reference) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -134,6 +171,19 @@ mpr_status mpr_lattice_torque(int n, const int* Lx, const int* Ly, const float* 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     return for_chunks(n, Lx, Ly, [&](const Grids& G, int k0, int m, int blocks) {
         lattice_torque_kernel<<<dim3(blocks, m), 256, 0, s>>>(G, k0, phi, (float)q, (float)J, g, grad);
+        return cudaGetLastError();
+    });
+}
+
+mpr_status mpr_lattice_grad(int n, const int* Lx, const int* Ly, const float* phi, double q,
+                            double J, const double* g, float* grad_phi, double* grad_J,
+                            mpr_stream stream) {
+    if (!phi || !g || (!grad_phi && !grad_J)) return MPR_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (grad_J && cudaMemsetAsync(grad_J, 0, sizeof(double), s) != cudaSuccess) return MPR_ERR_CUDA;
+    return for_chunks(n, Lx, Ly, [&](const Grids& G, int k0, int m, int blocks) {
+        lattice_grad_kernel<<<dim3(blocks, m), 256, 0, s>>>(G, k0, phi, (float)q, (float)J, g,
+                                                            grad_phi, grad_J);
         return cudaGetLastError();
     });
 }

@@ -4,9 +4,10 @@ The oracle cannot sweep these grids, so each test checks sampled outputs the
 oracle computes one by one: after one GPU sweep, a random sample of red gap
 sites is recomputed by the oracle's single-site update (Alg. 1) from the
 state before the sweep, and a random sample of black gap sites from the
-state after the red half (their neighbours are red).  Angles must agree
-within 1e-5 rad unless the oracle's decision lay within the FP32 error bound
-of its threshold.  Whole-grid properties are checked too: sample pixels
+state after the red half (their neighbours are red).  The decision-parity
+rule of tests/parity.py applies: angles within 1e-5 rad unless the oracle's
+decision lay within tolerance of its threshold (Metropolis: 1e-6), those
+counted and kept at or below 1e-4 of the sampled sites.  Whole-grid properties are checked too: sample pixels
 never move, gap angles stay in [0, 2 pi), the recorded energy equals the
 energy of the state, predictions at sample pixels return the data.
 """
@@ -17,6 +18,7 @@ import pytest
 
 import oracle
 import synthetic
+from parity import Tally
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -28,18 +30,6 @@ import paper_1710_03038_gb300 as mpr  # noqa: E402
 
 SEED = 0xFACE5EED
 N_SAMPLE = 400
-
-
-def _near(d):
-    """Decision within the FP32 error bound of its threshold (see test_gpu_parity)."""
-    bound = 1e-6 + d["ap"] * (d["sens"] * 2e-6 + abs(d["dH_over_T"]) * 1e-5)
-    return (abs(d["r_minus_ap"]) <= bound or d["or_slack"] < 1e-5 or d["wrap_slack"] < 1e-5
-            or d["field"] < 1e-5)
-
-
-def _within_1e6(d):
-    """The spec count: Metropolis decisions within 1e-6 of their threshold."""
-    return abs(d["r_minus_ap"]) < 1e-6
 
 
 def _neighbours(st, y, x):
@@ -64,7 +54,7 @@ def _check_sampled_sweep(ctx, gaps, T, rng):
     ctx.sweep(1, "equil", record_energy=True)
     after = ctx.get_state()
     info = ctx.chain_info()
-    n_checked = n_near = n_flip = n_1e6 = 0
+    tally = Tally()
     for i, g in enumerate(gaps):
         R = before[i].shape[0]
         Ly, Lx = g.shape
@@ -86,27 +76,14 @@ def _check_sampled_sweep(ctx, gaps, T, rng):
                 ref, _, diag = oracle.site_update(phi0, nb, x=x, y=y, T=float(T[i]),
                                                   a=float(a[i, c]), seed=SEED, img=i, chain=int(c),
                                                   sweep_index=sweep_idx)
-                got = float(after[i][c, y, x])
-                n_checked += 1
-                n_1e6 += _within_1e6(diag)
-                if _near(diag):
-                    n_near += 1
-                    n_flip += abs(got - ref) >= 1e-5
-                    continue
-                assert abs(got - ref) < 1e-5, (i, c, y, x, got, ref, diag)
+                tally.check_site(ref, float(after[i][c, y, x]), diag)
         # sample pixels never move, gap angles stay in [0, 2 pi)
         gm = torch.from_numpy(g.astype(bool)).cuda()
         assert torch.equal(after[i][:, ~gm], before[i][:, ~gm])
         ga = after[i][:, gm]
         assert bool((ga >= 0).all()) and bool((ga < 2 * math.pi + 1e-6).all())
-    # decisions within 1e-6 of threshold: below 1e-4 of the sampled sites
-    assert n_1e6 <= max(1, 1e-4 * n_checked), (n_1e6, n_checked)
-    # at the low temperatures of smooth fields the FP32 bound is wider; the
-    # decisions it covers may flip, and they must stay a small minority
-    assert n_near <= 0.05 * n_checked, (n_near, n_checked)
-    assert n_flip <= n_near
-    print(f"checked {n_checked} sites: {n_near} within the FP32 bound, {n_flip} flipped, "
-          f"{n_1e6} within 1e-6")
+    tally.assert_budget()
+    print(tally)
     return info
 
 

@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import synthetic
+from parity import Tally
 
 pytestmark = pytest.mark.gpu
 
@@ -47,22 +48,40 @@ def test_equilibrate_applies_the_slope_rule_and_matches_the_oracle():
     assert abs(hist[n - 1] - em[n_o - 1]) < 4e-3, (hist[n - 1], em[n_o - 1])
 
 
-def test_literal_over_relaxation_sweep_parity():
+def _sweep_parity(model_kw, oracle_sweep, path, R=4, T=0.13, sweeps=3):
+    """Three sweeps of a variant, each from the oracle's state, under the
+    decision-parity rule; returns the final GPU state."""
     z, g = _grf64()
-    ctx = mpr.Context([z], [g], chains=2, params=mpr.Params(seed=SEED, path="plain", literal_or=True))
-    ctx.set_T([0.13])
+    ctx = mpr.Context([z], [g], chains=R, params=mpr.Params(seed=SEED, path=path, **model_kw))
+    ctx.set_T([T])
     ctx.sweep(3, "equil")
-    before = ctx.get_state()[0].cpu().numpy()
-    a = ctx.chain_info()["a"][0]
-    s_idx, _ = ctx.sweep_index()
-    ctx.sweep(1, "equil")
-    after = ctx.get_state()[0].cpu().numpy()
-    for c in range(2):
-        ref, _, diag = oracle.sweep(before[c].astype(np.float64), g, T=0.13, a=float(a[c]),
-                                    seed=SEED, chain=c, sweep_index=s_idx, literal_or=True,
-                                    diagnostics=True)
-        d = np.abs(ref - after[c])[g == 1]
-        assert np.mean(d > 1e-5) < 0.01
+    tally = Tally()
+    state = ctx.get_state()[0].cpu().numpy().astype(np.float64)
+    for _ in range(sweeps):
+        ctx.set_state([state.astype(np.float32)])
+        before = state.astype(np.float32)
+        a = ctx.chain_info()["a"][0]
+        s_idx, _ = ctx.sweep_index()
+        ctx.sweep(1, "equil")
+        after = ctx.get_state()[0].cpu().numpy()
+        for c in range(R):
+            ref, _, diag = oracle_sweep(before[c].astype(np.float64), g, T=T, a=float(a[c]),
+                                        seed=SEED, chain=c, sweep_index=s_idx, diagnostics=True)
+            tally.check_grid(ref, after[c], g, diag)
+            assert np.array_equal(after[c][g == 0], before[c][g == 0])
+            state[c] = ref
+    tally.assert_budget()
+    print(tally)
+    ctx.set_state([state.astype(np.float32)])
+    ctx.sweep(2, "equil")
+    return [s.cpu().numpy() for s in ctx.get_state()]
+
+
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_literal_over_relaxation_sweep_parity(path):
+    """The printed (q = 1 field) over-relaxation, sweep by sweep, on both paths."""
+    fn = lambda *args, **kw: oracle.sweep(*args, literal_or=True, **kw)
+    _sweep_parity(dict(literal_or=True), fn, path)
 
 
 def test_literal_switches_bias_study():
@@ -175,28 +194,29 @@ def test_autotune_picks_a_valid_configuration():
         assert torch.equal(a, b)
 
 
-def test_gmrf_sweep_parity():
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_gmrf_sweep_parity(path):
+    """The GMRF variant of Sec. 4.3, sweep by sweep, on both paths."""
+    _sweep_parity(dict(model="gmrf"), oracle.gmrf_sweep, path, T=0.5)
+
+
+@pytest.mark.parametrize("variant", [dict(model="gmrf"), dict(literal_or=True)])
+def test_variants_tiled_equals_plain_bitwise(variant):
+    """The GMRF and printed-reflection instantiations of the tiled colour pass give the
+    plain path's bits (states, accepts, energies within FP32 summation order)."""
     z, g = _grf64()
-    ctx = mpr.Context([z], [g], chains=2, params=mpr.Params(seed=SEED, path="plain", model="gmrf"))
-    ctx.set_T([0.1])
-    ctx.sweep(3, "equil")
-    before = ctx.get_state()[0].cpu().numpy()
-    a = ctx.chain_info()["a"][0]
-    s_idx, _ = ctx.sweep_index()
-    ctx.sweep(1, "equil", record_energy=True)
-    after = ctx.get_state()[0].cpu().numpy()
-    e_rec = ctx.chain_info()["e_last"][0]
-    e_now = ctx.energy()[0]
-    for c in range(2):
-        ref, _, diag = oracle.gmrf_sweep(before[c].astype(np.float64), g, T=0.1, a=float(a[c]),
-                                         seed=SEED, chain=c, sweep_index=s_idx, diagnostics=True)
-        d = np.abs(ref - after[c])[g == 1]
-        assert np.mean(d > 1e-5) < 0.01
-        e_ref = oracle.gmrf_energy(after[c].astype(np.float64)) / oracle.n_bonds(64, 64)
-        assert abs(e_rec[c] - e_ref) < 2e-6 and abs(e_now[c] - e_ref) < 2e-6
-    info = ctx.image_info()
-    phi, _, _ = oracle.map_to_angles(z.astype(np.float64), g)
-    assert abs(info["e_s"][0] - oracle.gmrf_sample_energy(phi, g)[0]) < 1e-6
+    out = []
+    for path in ("plain", "tiled"):
+        ctx = mpr.Context([z], [g], chains=6, params=mpr.Params(seed=SEED, path=path, **variant))
+        ctx.set_T([0.3])
+        ctx.sweep(4, "equil", record_energy=True)
+        info = ctx.chain_info()
+        ctx.sweep(3, "measure")
+        out.append((ctx.get_state()[0].cpu().numpy(), info, ctx.predict()[0].cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1]["accepted"], out[1][1]["accepted"])
+    assert np.allclose(out[0][1]["e_last"], out[1][1]["e_last"], rtol=0, atol=1e-6)
+    assert np.allclose(out[0][2], out[1][2], rtol=1e-6, atol=1e-5)
 
 
 def test_mpr_beats_gmrf_on_lognormal_data():
