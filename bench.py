@@ -45,7 +45,7 @@ def _peaks():
 # Sources that determine the colour-pass kernel; the DRAM traffic recorded
 # from an ncu capture applies only while their hash is the recorded one.
 KERNEL_SOURCES = ("mpr_tiled_kernel.cuh", "mpr_device.cuh", "mpr_async.cuh", "mpr_internal.h")
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tiled_pass_kernel_lognormal2048.md")
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 def kernel_sources_hash():
@@ -58,17 +58,15 @@ def kernel_sources_hash():
 
 
 def recorded_traffic_per_update():
-    """DRAM bytes per gap site-update of the sampling colour pass from the committed ncu
-    summary, or None when the kernel sources changed since that capture."""
-    import re
-    if not os.path.exists(TRAFFIC_PROFILE):
+    """DRAM bytes per gap site-update of the sampling colour pass from the committed
+    record of an ncu capture, or None when the kernel sources changed since."""
+    if not os.path.exists(TRAFFIC_RECORD):
         return None
-    with open(TRAFFIC_PROFILE) as f:
-        m = re.search(r"traffic record: ([0-9.]+) B per gap site-update, kernel sources ([0-9a-f]+)",
-                      f.read())
-    if not m or m.group(2) != kernel_sources_hash():
+    with open(TRAFFIC_RECORD) as f:
+        rec = json.load(f)
+    if rec.get("kernel_sources_sha16") != kernel_sources_hash():
         return None
-    return float(m.group(1))
+    return float(rec["dram_bytes_per_gap_update"])
 
 
 def max_over_ranks(values, device):
@@ -170,28 +168,61 @@ def _crop(crop):
     return phi, g, int(w.gap[0].sum())
 
 
-def cpu_baseline(workers=None, crop=2048, sweeps=1, data=None):
-    """The FP64 oracle on the host cores: one sweep of a crop of the input per worker process."""
+def host_cpu():
+    """CPU model, logical cores and maximum clock of the host (lscpu, else /proc/cpuinfo)."""
+    info = {"cores": os.cpu_count() or 1}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            v = v.strip()
+            if k.strip() == "Model name" and "model" not in info:
+                info["model"] = v
+            elif k.strip() == "CPU max MHz":
+                info["max_mhz"] = float(v)
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    if "model" not in info and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                info["model"] = line.split(":", 1)[1].strip()
+                break
+    return info
+
+
+def cpu_baseline(workers=None, crop=2048, sweeps=1, data=None, single=True):
+    """The FP64 oracle on the host cores: one sweep of a crop of the input per worker
+    process on every core, and (single=True) the same work in one process alone."""
     import tempfile
     import numpy as np
     import oracle
     oracle.build()
-    workers = workers or min(os.cpu_count() or 1, 16)
+    workers = workers or (os.cpu_count() or 1)
     phi, g, _ = data if data is not None else _crop(crop)
+    ctx = mp.get_context("spawn")
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "crop.npz")
         np.savez(path, phi=phi, gap=g)
-        ctx = mp.get_context("spawn")
+        one = None
+        if single:
+            with ctx.Pool(1) as pool:
+                u1, s1 = pool.map(_oracle_worker, [(path, 0, sweeps)])[0]
+            one = u1 / s1
         t0 = time.perf_counter()
         with ctx.Pool(workers) as pool:
             res = pool.map(_oracle_worker, [(path, c, sweeps) for c in range(workers)])
         wall = time.perf_counter() - t0
     units = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
-    return {"value": units / busy, "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": f"{sweeps} hybrid sweep(s) of a {phi.shape[0]}x{phi.shape[1]} crop of the "
-                      f"4096^2 input, one realisation per worker, {workers} worker processes "
-                      f"({units} gap site-updates, {wall:.1f} s wall)", "wall_s": wall}
+    cpu = host_cpu()
+    out = {"value": units / busy, "unit": UNIT, "cores": workers, "kind": "oracle",
+           "sample": f"{sweeps} hybrid sweep(s) of a {phi.shape[0]}x{phi.shape[1]} crop of the "
+                     f"4096^2 input, one realisation per worker, {workers} worker processes "
+                     f"({units} gap site-updates, {wall:.1f} s wall)", "wall_s": wall,
+           "cpu": cpu}
+    if one is not None:
+        out["single_thread"] = {"value": one, "unit": UNIT, "cores": 1}
+    return out
 
 
 # ------------------------------------------------------------ GPU arm
@@ -389,7 +420,7 @@ def run_reference(args):
     vals, walls = [], []
     cb = None
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(crop=1024, data=data)
+        cb = cpu_baseline(crop=1024, data=data, single=False)
         if k >= args.warmup:
             vals.append(cb["value"])
             walls.append(cb["wall_s"])
@@ -449,6 +480,38 @@ def workload_rates(names):
         print(json.dumps(out), flush=True)
 
 
+def launch_ranks(n):
+    """--gpus N without a launcher: N local ranks through torch.distributed.run (one
+    process per GPU, RANK / LOCAL_RANK / WORLD_SIZE set for each), same arguments."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def dist_check(args):
+    """Host-side plumbing of a multi-rank run without GPU work: every rank reports a
+    timing, the slowest rank's counts, rank 0 prints one line (CPU ranks use gloo)."""
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("gloo")
+    ms = 100.0 + 10.0 * rank
+    ms_max = max_over_ranks([ms], torch.device("cpu"))[0]
+    value = job_throughput(1000, args.steps, ws, ms_max)
+    if ws > 1:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps({"check": "dist", "n_gpus": ws, "ms": ms_max, "value": value}), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -464,11 +527,17 @@ def main():
                     help="image side (4096 is the benchmark; smaller sides are for profiler captures)")
     ap.add_argument("--T", type=float, default=None,
                     help="fixed temperature instead of the estimate (profiler captures)")
+    ap.add_argument("--dist-check", action="store_true",
+                    help="check the multi-rank host logic without GPU work")
     ap.add_argument("--rates", nargs="*", default=None, metavar="WORKLOAD",
                     help="print the sweep rates of these synthetic workloads (all when none "
                          "is named) instead of the benchmark line")
     args = ap.parse_args()
-    if args.rates is not None:
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus))
+    if args.dist_check:
+        dist_check(args)
+    elif args.rates is not None:
         import synthetic
         workload_rates(args.rates or [n for n in synthetic.WORKLOADS if n != "grf64"])
     elif args.impl == "reference":

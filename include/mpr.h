@@ -318,21 +318,25 @@ mpr_status mpr_math_probe(int fn, int n, const float* a, const float* b, float* 
 
 /* ---- allocation-free entry point ------------------------------------------
  *
- * The sample specific energy of Eq. mpr-sse (with the sample extremes and
- * pair counts) for callers that may not allocate device memory at all: code
- * running where every byte of device memory belongs to another allocator (a
- * plugin inside a framework with its own memory pool), real-time pipelines
- * that forbid allocation once running, or hosts where an allocation would
- * synchronise the device.  The paper has no counterpart of this entry point;
- * it computes what mpr_init_grid() reports through mpr_get_image_info(), for
- * up to MPR_NOALLOC_MAX_IMAGES images per call.
+ * The sample specific energy (the mean of -J cos(q dphi) over the nearest-
+ * neighbour bonds whose both ends are samples, with the angles of the linear
+ * map of the sample values onto [0, 2 pi]), with the sample extremes and the
+ * number of such bonds, for callers that may not allocate device memory at
+ * all: code running where every byte of device memory belongs to another
+ * allocator (a plugin inside a framework with its own memory pool),
+ * real-time pipelines that forbid allocation once running, or hosts where an
+ * allocation would synchronise the device.  The paper has no counterpart of
+ * this entry point; for the MPR model it computes what mpr_init_grid()
+ * reports through mpr_get_image_info() (a GMRF context reports its own bond
+ * instead), for up to MPR_NOALLOC_MAX_IMAGES images per call.
  *
  * Inputs and outputs are the caller's: z, gap as for mpr_init_grid (device,
  * concatenated); e_s device [n_img] (nan when an image has fewer than two
- * distinct sample values or no sample pair); n_sp, z_min, z_max device
- * [n_img] or NULL.  Its temporary results go to a fixed array of about
- * 0.5 MB that this library reserves in every GPU's memory when it is loaded
- * (held until the process exits).  It calls no allocator.
+ * distinct sample values, no sample pair, or a non-finite sample value);
+ * n_sp, z_min, z_max device [n_img] or NULL.  Its temporary results go to a
+ * fixed array of about 0.5 MB that this library reserves in every GPU's
+ * memory when it is loaded (held until the process exits).  It calls no
+ * allocator.
  *  - The first call on a device looks the array's device address up (a
  *    cudaGetSymbolAddress); make that first call before any stream capture.
  *  - Every call on a device uses the same array: calls that may overlap on

@@ -477,29 +477,45 @@ def math_probe(fn: int, a: torch.Tensor, b: torch.Tensor = None) -> torch.Tensor
     return out
 
 
-def sample_energy_noalloc(z, gap, q: float = 0.5, J: float = 1.0, out=None, stream=None):
-    """e_s, N_SP, z_min, z_max per image without any allocation inside the library.
+def sample_energy_noalloc(z, gap, q: float = 0.5, J: float = 1.0, out=None, shapes=None,
+                          stream=None):
+    """e_s, N_SP, z_min, z_max per image from the library's allocation-free entry point.
 
-    z, gap: sequences of 2-D CUDA tensors (float32, uint8) or one concatenated
-    pair with ``shapes`` given through ``out``.  ``out`` may hold preallocated
-    device tensors dict(e_s=float64[n], n_sp=int64[n], zmin=float32[n],
-    zmax=float32[n]) so that the call itself allocates nothing.
+    z, gap: either one concatenated pair of 1-D CUDA tensors (float32 values,
+    uint8 mask, images in order) with ``shapes`` = [(Ly, Lx), ...], or
+    sequences of 2-D CUDA tensors.  With the concatenated form and a
+    preallocated ``out`` (dict of device tensors e_s float64[n], n_sp
+    int64[n], zmin float32[n], zmax float32[n]) neither the library nor this
+    wrapper allocates anything; the sequence form concatenates the images
+    first (a torch allocation, made on the stream the call runs on).
     """
-    zs, gs = _as_list(z), _as_list(gap)
-    shapes = [tuple(int(v) for v in g.shape) for g in gs]
+    st = stream if stream is not None else torch.cuda.current_stream()
+    if shapes is None:
+        zs, gs = _as_list(z), _as_list(gap)
+        shapes = [tuple(int(v) for v in g.shape) for g in gs]
+        with torch.cuda.stream(st):
+            zf = torch.cat([t.reshape(-1).to(torch.float32) for t in zs])
+            gf = torch.cat([(t.reshape(-1) != 0).to(torch.uint8) for t in gs])
+    else:
+        zf, gf = z, gap
+        if not (zf.is_contiguous() and gf.is_contiguous() and zf.dtype == torch.float32
+                and gf.dtype == torch.uint8):
+            raise ValueError("concatenated inputs must be contiguous float32 values and uint8 masks")
     n = len(shapes)
-    zf = zs[0] if n == 1 else torch.cat([t.reshape(-1) for t in zs])
-    gf = gs[0] if n == 1 else torch.cat([t.reshape(-1) for t in gs])
     if out is None:
         dev = zf.device
-        out = dict(e_s=torch.empty(n, dtype=torch.float64, device=dev),
-                   n_sp=torch.empty(n, dtype=torch.int64, device=dev),
-                   zmin=torch.empty(n, dtype=torch.float32, device=dev),
-                   zmax=torch.empty(n, dtype=torch.float32, device=dev))
+        with torch.cuda.stream(st):
+            out = dict(e_s=torch.empty(n, dtype=torch.float64, device=dev),
+                       n_sp=torch.empty(n, dtype=torch.int64, device=dev),
+                       zmin=torch.empty(n, dtype=torch.float32, device=dev),
+                       zmax=torch.empty(n, dtype=torch.float32, device=dev))
     call("mpr_sample_energy_noalloc", n, int_array([s[1] for s in shapes]),
-         int_array([s[0] for s in shapes]), _ptr(zf.contiguous()), _ptr(gf.contiguous()),
-         float(q), float(J), _ptr(out["e_s"]), _ptr(out["n_sp"]), _ptr(out["zmin"]),
-         _ptr(out["zmax"]), _stream_ptr(stream))
+         int_array([s[0] for s in shapes]), _ptr(zf), _ptr(gf), float(q), float(J),
+         _ptr(out["e_s"]), _ptr(out["n_sp"]), _ptr(out["zmin"]), _ptr(out["zmax"]),
+         _stream_ptr(st))
+    # keep the inputs alive until the kernels that read them have run
+    for t in (zf, gf):
+        t.record_stream(st)
     return out
 
 

@@ -1,5 +1,7 @@
-"""The benchmark's roofline traffic comes from the committed ncu summary of the
-colour pass, and only while the kernel sources are the ones that were profiled."""
+"""The benchmark's roofline traffic comes from the committed record of an ncu
+capture of the colour pass, and only while the kernel sources are the ones
+that were profiled."""
+import json
 import os
 import sys
 
@@ -9,24 +11,36 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_committed_record_is_read_for_its_kernel_sources(monkeypatch):
-    import re
-    with open(bench.TRAFFIC_PROFILE) as f:
-        m = re.search(r"traffic record: ([0-9.]+) B per gap site-update, kernel sources ([0-9a-f]+)",
-                      f.read())
-    assert m, "no traffic record line in the colour-pass summary"
-    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: m.group(2))
-    tpu = bench.recorded_traffic_per_update()
+def _write(path, tpu, sha):
+    with open(path, "w") as f:
+        json.dump({"dram_bytes_per_gap_update": tpu, "kernel_sources_sha16": sha}, f)
+
+
+def test_record_is_read_for_its_kernel_sources(monkeypatch, tmp_path):
+    rec = tmp_path / "traffic.json"
+    _write(rec, 12.5, bench.kernel_sources_hash())
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(rec))
+    assert bench.recorded_traffic_per_update() == 12.5
+
+
+def test_record_is_ignored_when_the_sources_change(monkeypatch, tmp_path):
+    rec = tmp_path / "traffic.json"
+    _write(rec, 12.5, "0" * 16)
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(rec))
+    assert bench.recorded_traffic_per_update() is None
+
+
+def test_record_is_ignored_without_a_record(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(tmp_path / "missing.json"))
+    assert bench.recorded_traffic_per_update() is None
+
+
+def test_committed_record_when_present_is_plausible():
+    if not os.path.exists(bench.TRAFFIC_RECORD):
+        return
+    with open(bench.TRAFFIC_RECORD) as f:
+        rec = json.load(f)
     # DRAM bytes per gap site-update: below the 14 B algorithmic figure plus the
     # realisation sums' share, and far above zero
-    assert tpu == float(m.group(1)) and 8.0 < tpu < 16.0
-
-
-def test_record_is_ignored_when_the_sources_change(monkeypatch):
-    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: "0" * 16)
-    assert bench.recorded_traffic_per_update() is None
-
-
-def test_record_is_ignored_without_a_summary(monkeypatch, tmp_path):
-    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(tmp_path / "missing.md"))
-    assert bench.recorded_traffic_per_update() is None
+    assert 6.0 < float(rec["dram_bytes_per_gap_update"]) < 20.0
+    assert len(rec["kernel_sources_sha16"]) == 16

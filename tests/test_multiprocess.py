@@ -57,3 +57,23 @@ def test_single_process_reduction_is_identity():
     import bench
     assert bench.max_over_ranks([1.5, 2.5], torch.device("cpu")) == [1.5, 2.5]
     assert bench.job_throughput(10, 2, 1, 1000.0) == pytest.approx(20.0)
+
+
+def test_gpus_flag_starts_one_rank_per_device_and_reduces():
+    """`bench.py --gpus 2` without a launcher starts two ranks (torch.distributed.run,
+    RANK / LOCAL_RANK / WORLD_SIZE per process); their host logic runs on gloo CPU
+    ranks here and rank 0 alone prints the line, with the slowest rank's time."""
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                          "--steps", "3", "--dist-check"], capture_output=True, text=True,
+                         timeout=300, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    assert lines[0]["n_gpus"] == 2 and lines[0]["ms"] == 110.0
+    assert lines[0]["value"] == pytest.approx(1000 * 3 * 2 / 0.110)

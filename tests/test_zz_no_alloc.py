@@ -52,6 +52,39 @@ def test_noalloc_sample_energy_matches_init_grid_twice():
         assert np.array_equal(got["zmax"].cpu().numpy(), ref["zmax"])
 
 
+def test_noalloc_concatenated_inputs_and_degenerate_images():
+    """The concatenated form (nothing allocated by the wrapper) on images without a
+    usable sample energy: constant sample values (z_max = z_min) and a checkerboard
+    mask (no sample pair) give e_s = nan and N_SP = 0; a regular image next to them
+    is unaffected."""
+    zc = torch.full((8, 8), 3.0, dtype=torch.float32, device="cuda")
+    gc = torch.zeros((8, 8), dtype=torch.uint8, device="cuda")
+    gc[0, 0] = 1
+    zk = torch.arange(64, dtype=torch.float32, device="cuda").reshape(8, 8)
+    yy, xx = torch.meshgrid(torch.arange(8), torch.arange(8), indexing="ij")
+    gk = ((xx + yy) % 2).to(torch.uint8).cuda()
+    zs, gs = _images()
+    zs, gs = [zc, zk, zs[0]], [gc, gk, gs[0]]
+    shapes = [tuple(t.shape) for t in gs]
+    zf = torch.cat([t.reshape(-1) for t in zs]).contiguous()
+    gf = torch.cat([t.reshape(-1) for t in gs]).contiguous()
+    n = len(zs)
+    out = dict(e_s=torch.empty(n, dtype=torch.float64, device="cuda"),
+               n_sp=torch.empty(n, dtype=torch.int64, device="cuda"),
+               zmin=torch.empty(n, dtype=torch.float32, device="cuda"),
+               zmax=torch.empty(n, dtype=torch.float32, device="cuda"))
+    for _ in range(2):
+        got = mpr.sample_energy_noalloc(zf, gf, out=out, shapes=shapes)
+        torch.cuda.synchronize()
+        e = got["e_s"].cpu().numpy()
+        nsp = got["n_sp"].cpu().numpy()
+        assert np.isnan(e[0]) and nsp[0] == 0
+        assert np.isnan(e[1]) and nsp[1] == 0
+        ref = mpr.Context([zs[2]], [gs[2]], chains=1).image_info()
+        assert np.allclose(e[2], ref["e_s"][0], rtol=1e-12, atol=1e-14)
+        assert nsp[2] == ref["n_sp"][0]
+
+
 def test_noalloc_rejects_more_images_than_its_scratch_holds():
     z = torch.zeros(4, dtype=torch.float32, device="cuda")
     g = torch.zeros(4, dtype=torch.uint8, device="cuda")
