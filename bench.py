@@ -69,6 +69,36 @@ def recorded_traffic_per_update():
     return float(rec["dram_bytes_per_gap_update"])
 
 
+def record_traffic(csv_path, size, command):
+    """Writes the traffic record from `ncu --page raw --csv` output of one sampling
+    launch of the colour pass (the kernel whose name carries the accumulate flag 1)
+    on the benchmark field at side `size`: DRAM bytes read + written per gap
+    site-update, and the kernel sources' hash at the time of writing."""
+    import csv
+    import synthetic
+    with open(csv_path) as f:
+        rows = list(csv.reader(l for l in f if not l.startswith("==")))
+    head, units = rows[0], rows[1]
+    k = head.index("Kernel Name")
+    hit = [r for r in rows[2:] if "tiled_pass_kernel<" in r[k] and ", 1, " in r[k]]
+    if not hit:
+        raise SystemExit("no sampling launch of the colour pass in " + csv_path)
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    tot = 0.0
+    for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        i = head.index(m)
+        tot += float(hit[0][i].replace(",", "")) * scale[units[i]]
+    w = synthetic.workload("lognormal4096", L=size)
+    updates = int(w.gap[0].sum()) * w.chains / 2.0
+    rec = {"dram_bytes_per_gap_update": round(tot / updates, 4),
+           "kernel": hit[0][k], "field_side": size, "updates_per_launch": updates,
+           "dram_bytes_per_launch": tot, "kernel_sources_sha16": kernel_sources_hash(),
+           "command": command}
+    with open(TRAFFIC_RECORD, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+
+
 def max_over_ranks(values, device):
     """Element-wise maximum of per-rank timings over all ranks (identity on one rank)."""
     import torch
@@ -529,13 +559,19 @@ def main():
                     help="fixed temperature instead of the estimate (profiler captures)")
     ap.add_argument("--dist-check", action="store_true",
                     help="check the multi-rank host logic without GPU work")
+    ap.add_argument("--record-traffic", default=None, metavar="NCU_RAW_CSV",
+                    help="write the roofline traffic record from `ncu --page raw --csv` output of "
+                         "one sampling launch captured on the field of side --size")
+    ap.add_argument("--ncu-command", default="", help="the capture's command, kept in the record")
     ap.add_argument("--rates", nargs="*", default=None, metavar="WORKLOAD",
                     help="print the sweep rates of these synthetic workloads (all when none "
                          "is named) instead of the benchmark line")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(launch_ranks(args.gpus))
-    if args.dist_check:
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.size, args.ncu_command)
+    elif args.dist_check:
         dist_check(args)
     elif args.rates is not None:
         import synthetic

@@ -37,7 +37,7 @@ typedef int mpr_status;
 #define MPR_ERR_CUDA             2  /* a CUDA runtime call failed                */
 #define MPR_ERR_DEGENERATE_RANGE 3  /* an image has z_max == z_min over samples  */
 #define MPR_ERR_NO_SAMPLE_PAIRS  4  /* no sample-sample bond: e_s undefined      */
-#define MPR_ERR_T_OUT_OF_RANGE   5  /* e_s outside (-J, -4J/pi^2)                 */
+#define MPR_ERR_T_OUT_OF_RANGE   5  /* e_s outside the range of e(T)              */
 #define MPR_ERR_WORKSPACE        6  /* workspace missing, misaligned or too small */
 #define MPR_ERR_STATE            7  /* call not valid in the context's state      */
 #define MPR_ERR_DEVICE           8  /* a kernel reported an error (status word)   */
@@ -166,7 +166,9 @@ mpr_status mpr_get_image_info(const mpr_ctx* ctx, double* e_s, int64_t* n_sp, in
  * bracket; every iteration re-equilibrates the lattices (warm start) and
  * averages n_meas sweeps over all chains.  The result becomes the context's
  * temperature.  T_out: host [n_img] (blocking) or NULL (asynchronous).
- * Errors: NO_SAMPLE_PAIRS, T_OUT_OF_RANGE (e_s >= -4J/pi^2 or <= -J). */
+ * Errors: NO_SAMPLE_PAIRS, T_OUT_OF_RANGE (e_s <= -J, or e_s at or above the
+ * infinite-temperature value: -J (sin(pi q) / (pi q))^2 for the MPR bond,
+ * -4J/pi^2 at q = 1/2; -2J/3 for the GMRF bond). */
 mpr_status mpr_estimate_T(mpr_ctx* ctx, double* T_out, mpr_stream stream);
 
 /* The equilibrium specific energy e(T, L) of Eq. ene as a table (Sec. 2.3:
@@ -187,6 +189,42 @@ mpr_status mpr_eT_table(int L, int n_T, const double* T, int chains, int n_equil
  * T_OUT_OF_RANGE when e_s lies outside the table, NO_SAMPLE_PAIRS. */
 mpr_status mpr_set_T_from_table(mpr_ctx* ctx, int n_T, const double* T, const double* e,
                                 double* T_out, mpr_stream stream);
+
+/* Cross-validated choice of the modification factor q for one Lx x Ly image.
+ * The conclusions name choosing q in (0, 1/2] by cross-validation, instead of
+ * fixing q = 1/2, as an extension of the method; the procedure here follows the
+ * paper's validation design (Sec. 3: a set-aside portion of the samples is the
+ * validation set, the absolute error averaged over it scores a prediction).
+ * For each candidate q[k] (host [n_q], each in (0, 1/2]):
+ *   1. the samples flagged in `holdout` become gaps next to the image's own
+ *      gaps (flags on gap pixels are ignored); the angle map uses the extremes
+ *      of the remaining samples;
+ *   2. the gap fill of Alg. 2 at q[k] with the parameters p (seed included, the
+ *      same for every candidate): sample specific energy of the remaining
+ *      samples, SEM temperature (mpr_estimate_T with T_opts), n_equil
+ *      equilibration and n_meas sampling sweeps of n_chains realisations,
+ *      prediction;
+ *   3. scores[k] = mean over validation points of |z_hat - z| (FP64 sum).
+ * A candidate with no SEM temperature (e_s outside the range of e(T) at that q)
+ * scores +inf and gets T_out[k] = nan.  *q_best (nullable) receives the first
+ * candidate with the smallest score; T_out (nullable, host [n_q]) the SEM
+ * temperatures.
+ *  z, gap, holdout  [Lx*Ly] float / uint8 / uint8 (nonzero = validation
+ *                   point), host or device as `where` says
+ *  p                p->model must be MPR_MODEL_MPR and p->literal_or 0
+ *  workspace        caller-owned device memory of
+ *                   mpr_select_q_workspace_size() bytes, 256-byte aligned; it
+ *                   holds one context at a time and the staged inputs
+ * Blocking.  Errors: INVALID_ARG (bad sizes, q outside (0, 1/2], no validation
+ * point), WORKSPACE, DEGENERATE_RANGE / NO_SAMPLE_PAIRS from the init of the
+ * reduced sample set, T_OUT_OF_RANGE when no candidate has a SEM temperature. */
+mpr_status mpr_select_q_workspace_size(int Lx, int Ly, int n_chains, const mpr_params* p,
+                                       const mpr_T_opts* T_opts, size_t* bytes);
+mpr_status mpr_select_q(int Lx, int Ly, const float* z, const uint8_t* gap, const uint8_t* holdout,
+                        mpr_mem where, int n_q, const double* q, int n_chains, int n_equil,
+                        int n_meas, const mpr_params* p, const mpr_T_opts* T_opts, void* workspace,
+                        size_t ws_bytes, double* scores, double* T_out, double* q_best,
+                        mpr_stream stream);
 
 /* Sets / reads the reduced temperature of every image (host [n_img]). */
 mpr_status mpr_set_T(mpr_ctx* ctx, const double* T, mpr_stream stream);

@@ -12,6 +12,7 @@ for the readings of the paper that it takes.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -278,6 +279,50 @@ def fill(z, gap, *, R, n_equil, n_meas, seed, img=0, T=None, sem=None, q=0.5, J=
     z_hat = np.where(np.asarray(gap) != 0, unmap(sim["phi_mean"], zmin, zmax),
                      np.asarray(z, dtype=np.float64))
     return dict(z_hat=z_hat, T=T, e_s=e_s, zmin=zmin, zmax=zmax)
+
+
+def select_q(z, gap, holdout, qs, *, R, n_equil, n_meas, seed, sem, img=0, J=1.0,
+             A_targ=0.3, k_a=3.0, freeze_a=True):
+    """Cross-validated choice of the modification factor q (the conclusions name the
+    selection of q in (0, 1/2] by cross-validation as an extension of the method).
+
+    Steps, for every candidate q in ``qs`` (each in (0, 1/2]):
+      1. the samples flagged in ``holdout`` are set aside as a validation set, as in
+         Sec. 3's validation design: they become gaps next to the image's own gaps,
+         and the angle map uses the extremes of the remaining samples;
+      2. the whole gap fill of Alg. 2 at that q: sample specific energy of the
+         remaining samples, SEM temperature (Sec. 2.3), conditional simulation of R
+         realisations with the same seed for every q, realisation mean, back-transform;
+      3. the score is the absolute error averaged over the validation points (AAE of
+         Sec. 3) of that prediction.
+    The chosen q is the first candidate with the smallest score.  A candidate whose
+    sample specific energy lies outside the range of e(T) scores infinity (T = nan).
+    A holdout flag on a gap pixel is ignored.  Returns dict(q, scores, T).
+    """
+    z = np.asarray(z, dtype=np.float64)
+    g = np.asarray(gap) != 0
+    hold = (np.asarray(holdout) != 0) & ~g
+    if not hold.any():
+        raise ValueError("no held-out sample")
+    g_cv = (g | hold).astype(np.uint8)
+    scores, Ts = [], []
+    for q in qs:
+        if not 0.0 < q <= 0.5:
+            raise ValueError("q must lie in (0, 1/2]")
+        try:
+            r = fill(z, g_cv, R=R, n_equil=n_equil, n_meas=n_meas, seed=seed, img=img, sem=sem,
+                     q=q, J=J, A_targ=A_targ, k_a=k_a, freeze_a=freeze_a)
+        except ValueError:
+            # e_s outside the range of e(T) at this q: no SEM temperature exists
+            scores.append(math.inf)
+            Ts.append(math.nan)
+            continue
+        scores.append(float(np.mean(np.abs(r["z_hat"][hold] - z[hold]))))
+        Ts.append(r["T"])
+    if not np.isfinite(scores).any():
+        raise ValueError("no candidate q has a SEM temperature")
+    k = int(np.argmin(scores))
+    return dict(q=float(qs[k]), scores=np.array(scores), T=np.array(Ts))
 
 
 def sg_slope(y):

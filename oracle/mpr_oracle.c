@@ -364,13 +364,16 @@ double oracle_e_of_T(int L, int K, int n_eq, int n_meas, double q, double J, dou
 /* T_hat = e^-1(e_s | L) (Sec. 2.3) by bisection on log T inside
  * [T_lo, T_hi], using that e(T) increases with T.  Every evaluation of
  * e(T) uses the same random stream.  Stops when (T_hi - T_lo)/T_mid < rel_tol
- * or after max_iter halvings.  Returns 0; -1 when e_s lies outside
- * (-J, -4J/pi^2), the range of e(T) between T = 0 and T = infinity. */
+ * or after max_iter halvings.  Returns 0; -1 when e_s lies outside the
+ * range of e(T) between T = 0 (aligned spins, -J) and T = infinity
+ * (independent uniform angles: <cos(q dphi)> = (sin(pi q) / (pi q))^2, so
+ * -J (sin(pi q) / (pi q))^2, which is -4J/pi^2 at q = 1/2). */
 int oracle_estimate_T(double e_s, int L, int K, int n_eq, int n_meas, double q, double J,
                       double A_targ, double k_a, uint64_t seed, uint32_t img,
                       double T_lo, double T_hi, double rel_tol, int max_iter, double* T_out)
 {
-    if (!(e_s > -J && e_s < -4.0 * J / (OR_PI * OR_PI))) return -1;
+    const double sq = sin(OR_PI * q) / (OR_PI * q);
+    if (!(e_s > -J && e_s < -J * sq * sq)) return -1;
     double lo = log(T_lo), hi = log(T_hi);
     for (int it = 0; it < max_iter; ++it) {
         double mid = 0.5 * (lo + hi);

@@ -380,6 +380,37 @@ def eT_table(T_grid, L: int = 256, chains: int = 16, n_equil: int = 60, n_meas: 
     return np.array(e[:]), np.array(v[:])
 
 
+def select_q(z, gap, holdout, qs, chains: int = 16, n_equil: int = 100, n_meas: int = 100,
+             params: Params = None, topts: TOpts = None, device=None, stream=None):
+    """Cross-validated q (mpr_select_q): the samples flagged in `holdout` are the
+    validation set; every candidate q runs the gap fill and is scored by the mean
+    absolute error at the validation points -> dict(q, scores, T)."""
+    params = params or Params()
+    topts = topts or TOpts()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    zt = torch.as_tensor(np.asarray(z) if not torch.is_tensor(z) else z).to(dev, torch.float32).contiguous()
+    gt = torch.as_tensor(np.asarray(gap) if not torch.is_tensor(gap) else gap).to(dev, torch.uint8).contiguous()
+    ht = torch.as_tensor(np.asarray(holdout) if not torch.is_tensor(holdout) else holdout)
+    ht = ht.to(dev, torch.uint8).contiguous()
+    Ly, Lx = zt.shape
+    if tuple(gt.shape) != (Ly, Lx) or tuple(ht.shape) != (Ly, Lx):
+        raise ValueError("z, gap and holdout must have one shape")
+    pc, tc = params.c(), topts.c()
+    nbytes = C.c_size_t()
+    call("mpr_select_q_workspace_size", int(Lx), int(Ly), int(chains), C.byref(pc), C.byref(tc),
+         C.byref(nbytes))
+    ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+    n = len(qs)
+    qa = (C.c_double * n)(*[float(v) for v in qs])
+    sc = (C.c_double * n)()
+    Ts = (C.c_double * n)()
+    qb = C.c_double()
+    call("mpr_select_q", int(Lx), int(Ly), _ptr(zt), _ptr(gt), _ptr(ht), _lib.MPR_DEVICE, n, qa,
+         int(chains), int(n_equil), int(n_meas), C.byref(pc), C.byref(tc), _ptr(ws),
+         C.c_size_t(ws.numel()), sc, Ts, C.byref(qb), _stream_ptr(stream))
+    return dict(q=qb.value, scores=np.array(sc[:]), T=np.array(Ts[:]))
+
+
 def fill(z, gap, chains: int, n_equil: int, n_meas: int, params: Params = None,
          topts: TOpts = None, T=None, std: bool = False):
     """Whole gap fill (Alg. 2): init, SEM temperature (unless T given), sweeps, prediction."""

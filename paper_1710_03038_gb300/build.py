@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmpr.so")
 SOURCES = ["mpr_api.cu", "mpr_tiled.cu", "mpr_tiled_32x16.cu", "mpr_tiled_16x16.cu",
            "mpr_tiled_16x16_lit.cu", "mpr_tiled_16x16_gmrf.cu",
-           "mpr_tiled_32x32.cu", "mpr_plain.cu", "mpr_lattice.cu", "mpr_noalloc.cu"]
+           "mpr_tiled_32x32.cu", "mpr_plain.cu", "mpr_lattice.cu", "mpr_noalloc.cu",
+           "mpr_qcv.cu"]
 HEADERS = ["mpr_device.cuh", "mpr_internal.h", "mpr_async.cuh", "mpr_tiled_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC",

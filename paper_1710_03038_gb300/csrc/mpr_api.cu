@@ -142,7 +142,7 @@ Layout make_layout(const Geometry& g, const std::vector<long long>& slots_per_im
     L.acc2 = take(sizeof(double) * L.n_slots);
     L.state = take(sizeof(float) * L.n_state);
     L.newton = take(sizeof(double) * 4 * g.n_img);
-    L.hist = take(sizeof(double) * kHist * g.n_img + sizeof(int) * (g.n_img + 1));
+    L.hist = take(sizeof(double) * kHist * g.n_img + sizeof(int) * (g.n_img + 3));
     L.sub = take(sub_bytes);
     L.total = o;
     return L;
@@ -193,7 +193,8 @@ struct mpr_ctx {
     double* d_eout = nullptr;
     double* d_newton = nullptr;
     double* d_hist = nullptr;     // [n_img][kHist] chain-mean specific energy per sweep (ring)
-    int* d_sg = nullptr;          // [n_img] image settled, [n_img] = images still settling
+    int* d_sg = nullptr;          // [n_img] image settled; then images still settling after the
+                                  // last check, sweeps done, 1 once every image settled
     // host mirrors
     std::vector<ImgDev> h_img;
     std::vector<long long> slots;
@@ -208,8 +209,13 @@ struct mpr_ctx {
     mpr_ctx* sub = nullptr;   // unconditional lattices of the temperature estimate
     // instantiated CUDA graphs of sweep sequences, keyed by (n, phase, flags, stats, accumulate)
     std::vector<std::pair<long long, cudaGraphExec_t>> graphs;
+    // the equilibration with its stop rule as one device-side while loop, keyed by
+    // (n_f, n_fit, i_max)
+    cudaGraphExec_t eq_exec = nullptr;
+    long long eq_key = -1;
     ~mpr_ctx() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+        if (eq_exec) cudaGraphExecDestroy(eq_exec);
         delete sub;
     }
 };
@@ -414,8 +420,8 @@ __global__ void set_alpha_kernel(ChainDev ch, int nc) {
 }
 
 // Bookkeeping after every sweep: acceptance -> a (Alg. 2 step 4.2), energy
-// record (step 4.3), counters.  One block; one warp per chain at a time sums
-// the chain's kSpread partial slots.
+// record (step 4.3), counters.  One warp per chain sums the chain's kSpread
+// partial slots; the warps of all blocks share the chains.
 __global__ void end_sweep_kernel(const ImgDev* img, ChainDev ch, Control* ctl, int n_img,
                                  int n_chains, int equil, int record, int stats, int add_ess,
                                  double A_targ, double k_a) {
@@ -423,7 +429,8 @@ __global__ void end_sweep_kernel(const ImgDev* img, ChainDev ch, Control* ctl, i
     const uint32_t i = ctl->equil_index;
     const int nc = n_img * n_chains;
     const int lane = threadIdx.x & 31;
-    for (int c = threadIdx.x >> 5; c < nc; c += blockDim.x >> 5) {
+    const int wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nc; c += gridDim.x * wpb) {
         const ImgDev& I = img[c / n_chains];
         uint32_t cnt = ch.acc_cnt[c * kSpread + lane];
         double e_gap = ch.e_cur[c * kSpread + lane];
@@ -448,10 +455,16 @@ __global__ void end_sweep_kernel(const ImgDev* img, ChainDev ch, Control* ctl, i
             ch.e_last[c] = __longlong_as_double(0x7FF8000000000000LL);
         }
     }
+    // the last block to finish advances the counters: every block has read
+    // equil_index before it takes its ticket
     __syncthreads();
     if (threadIdx.x == 0) {
-        ctl->sweep += 1;
-        if (equil) ctl->equil_index += 1;
+        __threadfence();
+        if (atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1) {
+            ctl->ticket = 0;
+            ctl->sweep += 1;
+            if (equil) ctl->equil_index += 1;
+        }
     }
 }
 
@@ -619,40 +632,56 @@ __global__ void acc_dense_kernel(const ImgDev* img, double* acc, const int* slot
 }
 
 // Chain-mean specific energy of every image after sweep i, into its ring.
-__global__ void sg_record_kernel(const ChainDev ch, double* hist, int n_img, int n_chains,
-                                 uint32_t i) {
-    const int im = blockIdx.x * blockDim.x + threadIdx.x;
-    if (im >= n_img) return;
-    double s = 0.0;
-    for (int k = 0; k < n_chains; ++k) s += ch.e_last[im * n_chains + k];
-    hist[(size_t)im * kHist + (i % kHist)] = s / n_chains;
-}
-
-// Savitzky-Golay slope of degree 1 (the least-squares line) through the last
-// n_fit chain-mean energies of every image, ending at sweep i; an image whose
-// slope is no longer negative has settled (Alg. 2 step 4.4).  sg[n_img]
-// receives how many images are still settling.
-__global__ void sg_check_kernel(const double* hist, int* sg, int n_img, int n_fit, uint32_t i) {
+// Alg. 2 step 4.4 after the equilibration sweep i that just ran (i read from
+// sg[n_img + 1]): records the chain-mean specific energy of every image in the
+// ring hist; at a check sweep (i >= n_fit and i mod n_f == 0) fits the
+// least-squares line (a degree-1 Savitzky-Golay filter) through the last n_fit
+// entries of every image still settling and marks an image settled once its
+// slope is no longer negative.  sg: [n_img] settled flags (sticky), then the
+// images still settling after the last check, the sweeps done, and 1 once every
+// image settled.  With use_h the kernel also sets the conditional handle h to
+// whether another sweep follows (not once every image settled, nor after sweep
+// i_max); h ends the device-side while loop, which therefore runs at most
+// i_max + 1 times.  One block.
+__global__ void sg_step_kernel(const ChainDev ch, double* hist, int* sg, int n_img, int n_chains,
+                               int n_fit, int n_f, int i_max, cudaGraphConditionalHandle h,
+                               int use_h) {
     __shared__ int unsettled;
+    const uint32_t i = (uint32_t)sg[n_img + 1];
     if (threadIdx.x == 0) unsettled = 0;
-    __syncthreads();
     for (int im = threadIdx.x; im < n_img; im += blockDim.x) {
-        if (sg[im]) continue;
-        const double xm = 0.5 * (n_fit - 1);
-        double ym = 0.0;
-        for (int k = 0; k < n_fit; ++k) ym += hist[(size_t)im * kHist + ((i + 1 + k - n_fit) % kHist)];
-        ym /= n_fit;
-        double sxy = 0.0, sxx = 0.0;
-        for (int k = 0; k < n_fit; ++k) {
-            const double y = hist[(size_t)im * kHist + ((i + 1 + k - n_fit) % kHist)];
-            sxy += (k - xm) * (y - ym);
-            sxx += (k - xm) * (k - xm);
-        }
-        if (sxy / sxx >= 0.0) sg[im] = 1;
-        else atomicAdd(&unsettled, 1);
+        double s = 0.0;
+        for (int k = 0; k < n_chains; ++k) s += ch.e_last[(size_t)im * n_chains + k];
+        hist[(size_t)im * kHist + (i % kHist)] = s / n_chains;
     }
     __syncthreads();
-    if (threadIdx.x == 0) sg[n_img] = unsettled;
+    const bool check = i >= (uint32_t)n_fit && i % (uint32_t)n_f == 0;
+    if (check) {
+        for (int im = threadIdx.x; im < n_img; im += blockDim.x) {
+            if (sg[im]) continue;
+            const double xm = 0.5 * (n_fit - 1);
+            double ym = 0.0;
+            for (int k = 0; k < n_fit; ++k)
+                ym += hist[(size_t)im * kHist + ((i + 1 + k - n_fit) % kHist)];
+            ym /= n_fit;
+            double sxy = 0.0, sxx = 0.0;
+            for (int k = 0; k < n_fit; ++k) {
+                const double y = hist[(size_t)im * kHist + ((i + 1 + k - n_fit) % kHist)];
+                sxy += (k - xm) * (y - ym);
+                sxx += (k - xm) * (k - xm);
+            }
+            if (sxy / sxx >= 0.0) sg[im] = 1;
+            else atomicAdd(&unsettled, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool stop = check && unsettled == 0;
+        if (check) sg[n_img] = unsettled;
+        sg[n_img + 1] = (int)(i + 1);
+        sg[n_img + 2] = stop ? 1 : 0;
+        if (use_h) cudaGraphSetConditional(h, (!stop && i + 1 <= (uint32_t)i_max) ? 1u : 0u);
+    }
 }
 
 __global__ void set_T_kernel(ImgDev* img, const double* T, int n) {
@@ -1149,12 +1178,40 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
             }
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
         }
-        end_sweep_kernel<<<1, 1024, 0, s>>>(c->d_img, c->ch, c->d_ctl, c->g.n_img, c->g.n_chains,
-                                           equil ? 1 : 0, record ? 1 : 0, stats ? 1 : 0,
-                                           tiled ? 1 : 0, c->p.A_targ, c->p.k_a);
+        // one warp per chain, 8 chains per block
+        const int nc = c->g.n_img * c->g.n_chains;
+        end_sweep_kernel<<<std::min((nc + 7) / 8, 1024), 256, 0, s>>>(
+            c->d_img, c->ch, c->d_ctl, c->g.n_img, c->g.n_chains, equil ? 1 : 0, record ? 1 : 0,
+            stats ? 1 : 0, tiled ? 1 : 0, c->p.A_targ, c->p.k_a);
         MPR_CUDA(cudaGetLastError());
     }
     return MPR_OK;
+}
+
+// Launch settings that may not change during a stream capture (the colour
+// passes' shared-memory attributes) are applied before one begins.
+mpr_status prepare_capture(mpr_ctx* c, cudaStream_t s) {
+    if (c->g.path != MPR_PATH_TILED) return MPR_OK;
+    SweepArgs a{};
+    a.n_chains = c->g.n_chains;
+    a.flags = model_flags(c->p);
+    ChainRange cr[2];
+    const int n_cr = chain_ranges(c, cr);
+    for (int r = 0; r < n_cr; ++r) {
+        a.chain0 = cr[r].chain0;
+        a.chain_end = cr[r].chain_end;
+        a.chain_group = cr[r].group;
+        MPR_CUDA(launch_tiled_pass(a, c->g.tx, c->g.ty, s, true));
+    }
+    return MPR_OK;
+}
+
+// Whether runs of sweeps on stream s may go through CUDA graphs: graphs are
+// enabled, the stream is not the legacy one and nobody is capturing it.
+bool graphs_usable(const mpr_ctx* c, cudaStream_t s) {
+    if (!c->p.use_graphs || s == nullptr || s == cudaStreamLegacy) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
 }
 
 // n sweeps: launched directly, or (sequences of at least 4 sweeps on a stream
@@ -1164,12 +1221,8 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
 // stays valid.
 mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool accumulate,
                       cudaStream_t s) {
-    bool graph = c->p.use_graphs && n >= 4 && s != nullptr && s != cudaStreamLegacy;
-    if (graph) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-            graph = false;  // the caller is capturing: launch into the caller's capture
-    }
+    // (a caller that is capturing gets the launches in its own capture)
+    const bool graph = n >= 4 && graphs_usable(c, s);
     if (!graph) {
         MPR_TRY(launch_sweeps(c, n, phase, flags, stats, accumulate, s));
     } else {
@@ -1179,19 +1232,7 @@ mpr_status run_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bool 
         for (auto& g : c->graphs)
             if (g.first == key) exec = g.second;
         if (!exec) {
-            if (c->g.path == MPR_PATH_TILED) {
-                SweepArgs a{};
-                a.n_chains = c->g.n_chains;
-                a.flags = model_flags(c->p);
-                ChainRange cr[2];
-                const int n_cr = chain_ranges(c, cr);
-                for (int r = 0; r < n_cr; ++r) {
-                    a.chain0 = cr[r].chain0;
-                    a.chain_end = cr[r].chain_end;
-                    a.chain_group = cr[r].group;
-                    MPR_CUDA(launch_tiled_pass(a, c->g.tx, c->g.ty, s, true));
-                }
-            }
+            MPR_TRY(prepare_capture(c, s));
             MPR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
             const mpr_status st = launch_sweeps(c, n, phase, flags, stats, accumulate, s);
             cudaGraph_t g = nullptr;
@@ -1390,9 +1431,11 @@ mpr_status mpr_estimate_T(mpr_ctx* c, double* T_out, mpr_stream stream) {
     for (int i = 0; i < c->g.n_img; ++i) {
         const ImgDev& I = c->h_img[i];
         if (I.n_sp == 0) return fail(MPR_ERR_NO_SAMPLE_PAIRS, "image " + std::to_string(i) + " has no sample pairs");
-        // e(T) runs from -J (T = 0) to the independent-angle value: -4J/pi^2 for
-        // the MPR bond, J (1/3 - 1) for the GMRF bond
-        const double e_inf = c->p.model == MPR_MODEL_GMRF ? -2.0 * J / 3.0 : -4.0 * J / (kPiD * kPiD);
+        // e(T) runs from -J (T = 0) to the independent-angle value: for the MPR
+        // bond -J <cos(q dphi)> = -J (sin(pi q) / (pi q))^2 (-4J/pi^2 at q = 1/2),
+        // for the GMRF bond J (<dphi^2> / (2 pi^2) - 1) = -2J/3
+        const double sq = std::sin(kPiD * c->p.q) / (kPiD * c->p.q);
+        const double e_inf = c->p.model == MPR_MODEL_GMRF ? -2.0 * J / 3.0 : -J * sq * sq;
         if (!(I.e_s > -J && I.e_s < e_inf))
             return fail(MPR_ERR_T_OUT_OF_RANGE, "image " + std::to_string(i) +
                                                     ": e_s outside the range of e(T)");
@@ -1574,22 +1617,71 @@ mpr_status mpr_equilibrate(mpr_ctx* c, int n_f, int n_fit, int i_max, int* n_don
     if (!c->T_set) return fail(MPR_ERR_STATE, "temperature not set: call mpr_estimate_T or mpr_set_T");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int n_img = c->g.n_img;
-    MPR_CUDA(cudaMemsetAsync(c->d_sg, 0, sizeof(int) * (n_img + 1), s));
+    MPR_CUDA(cudaMemsetAsync(c->d_sg, 0, sizeof(int) * (n_img + 3), s));
     int done = 0;
-    for (int i = 0; i <= i_max; ++i) {
-        // sweep i of this equilibration (Alg. 2 step 4.1-4.3), energies recorded
-        MPR_TRY(run_sweeps(c, 1, MPR_EQUIL, MPR_RECORD_ENERGY, false, true, s));
-        sg_record_kernel<<<grid_for(n_img), 256, 0, s>>>(c->ch, c->d_hist, n_img, c->g.n_chains,
-                                                          (uint32_t)i);
-        MPR_CUDA(cudaGetLastError());
-        done = i + 1;
-        if (i >= n_fit && i % n_f == 0) {
-            sg_check_kernel<<<1, 256, 0, s>>>(c->d_hist, c->d_sg, n_img, n_fit, (uint32_t)i);
+    if (graphs_usable(c, s)) {
+        // the whole run as one graph: a while node whose body is one sweep and the
+        // stop rule, which sets the loop's condition on the device (no host round
+        // trip per check)
+        const long long key = ((long long)n_f << 42) | ((long long)n_fit << 32) | (long long)i_max;
+        if (!c->eq_exec || c->eq_key != key) {
+            if (c->eq_exec) cudaGraphExecDestroy(c->eq_exec);
+            c->eq_exec = nullptr;
+            MPR_TRY(prepare_capture(c, s));
+            cudaGraph_t g = nullptr;
+            MPR_CUDA(cudaGraphCreate(&g, 0));
+            cudaGraphConditionalHandle h;
+            cudaGraphNode_t node;
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+            if (e == cudaSuccess) {
+                np.conditional.handle = h;
+                np.conditional.type = cudaGraphCondTypeWhile;
+                np.conditional.size = 1;
+                e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+            }
+            mpr_status st = MPR_OK;
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(s, np.conditional.phGraph_out[0], nullptr, nullptr,
+                                                  0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                st = launch_sweeps(c, 1, MPR_EQUIL, MPR_RECORD_ENERGY, false, true, s);
+                if (st == MPR_OK) {
+                    sg_step_kernel<<<1, 256, 0, s>>>(c->ch, c->d_hist, c->d_sg, n_img, c->g.n_chains,
+                                                     n_fit, n_f, i_max, h, 1);
+                    e = cudaGetLastError();
+                }
+                cudaGraph_t body = nullptr;
+                const cudaError_t ee = cudaStreamEndCapture(s, &body);
+                if (e == cudaSuccess) e = ee;
+            }
+            if (st == MPR_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->eq_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (st != MPR_OK) return st;
+            if (e != cudaSuccess)
+                return fail(MPR_ERR_CUDA, std::string("equilibration graph: ") + cudaGetErrorString(e));
+            c->eq_key = key;
+        }
+        MPR_CUDA(cudaGraphLaunch(c->eq_exec, s));
+        MPR_CUDA(cudaMemcpyAsync(&done, c->d_sg + n_img + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MPR_CUDA(cudaStreamSynchronize(s));
+        c->sweep += (uint32_t)done;
+        c->equil_index += (uint32_t)done;
+    } else {
+        for (int i = 0; i <= i_max; ++i) {
+            // sweep i of this equilibration (Alg. 2 step 4.1-4.3), energies recorded
+            MPR_TRY(run_sweeps(c, 1, MPR_EQUIL, MPR_RECORD_ENERGY, false, true, s));
+            sg_step_kernel<<<1, 256, 0, s>>>(c->ch, c->d_hist, c->d_sg, n_img, c->g.n_chains, n_fit,
+                                             n_f, i_max, cudaGraphConditionalHandle{}, 0);
             MPR_CUDA(cudaGetLastError());
-            int unsettled = 0;
-            MPR_CUDA(cudaMemcpyAsync(&unsettled, c->d_sg + n_img, sizeof(int), cudaMemcpyDeviceToHost, s));
-            MPR_CUDA(cudaStreamSynchronize(s));
-            if (unsettled == 0) break;
+            done = i + 1;
+            if (i >= n_fit && i % n_f == 0) {
+                int stop = 0;
+                MPR_CUDA(cudaMemcpyAsync(&stop, c->d_sg + n_img + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+                MPR_CUDA(cudaStreamSynchronize(s));
+                if (stop) break;
+            }
         }
     }
     if (n_done) *n_done = done;

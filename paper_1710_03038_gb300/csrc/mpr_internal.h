@@ -50,7 +50,7 @@ struct Control {
     uint32_t sweep;        // Philox sweep field of the next sweep
     uint32_t equil_index;  // i of Alg. 2 step 4.2 for the next equilibration sweep
     uint32_t status;       // device-side error bits
-    uint32_t pad;
+    uint32_t ticket;       // blocks of the end-of-sweep kernel done (0 between launches)
 };
 
 // Accept counts and energy partials of a chain are spread over kSpread

@@ -1,4 +1,5 @@
-"""Rows after the hot path: automatic equilibration stop and the paper-literal switches."""
+"""Rows after the hot path: automatic equilibration stop, the paper-literal switches,
+the GMRF variant, the e(T) table, batching, autotuning and the cross-validated q."""
 import math
 
 import numpy as np
@@ -46,6 +47,40 @@ def test_equilibrate_applies_the_slope_rule_and_matches_the_oracle():
     # the stopping sweep and the energy reached agree statistically
     assert abs(n - n_o) <= 60, (n, n_o)
     assert abs(hist[n - 1] - em[n_o - 1]) < 4e-3, (hist[n - 1], em[n_o - 1])
+
+
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_equilibrate_device_stop_equals_host_loop(path):
+    """On a side stream the equilibration runs as one graph whose while loop the stop
+    rule ends on the device; on the legacy stream the host reads the rule's flag at
+    every check.  Both stop after the same sweep with the same bits, for a stop by
+    the rule and for a stop at i_max."""
+    zs, gs = [], []
+    for k, (h, w) in enumerate([(64, 64), (40, 90)]):
+        zs.append(synthetic.grf((h, w), nu=0.5, ell=6.0, mean=50, std=10, seed=900 + k).astype(np.float32))
+        gs.append(synthetic.uniform_gaps((h, w), 0.4, 910 + k).astype(np.uint8))
+    side = torch.cuda.Stream()
+    for i_max in (300, 15):
+        res = []
+        for stream in (None, side):
+            ctx = mpr.Context(zs, gs, chains=6, params=mpr.Params(seed=SEED, path=path))
+            ctx.set_T([0.13, 0.2])
+            n = ctx.equilibrate(n_f=5, n_fit=20, i_max=i_max, stream=stream)
+            torch.cuda.synchronize()
+            res.append((n, ctx.energy_history()[:, :n].copy(), [t.cpu().numpy() for t in ctx.get_state()],
+                        ctx.sweep_index()))
+            # a second run of the same length reuses the instantiated graph
+            if stream is side:
+                n2 = ctx.equilibrate(n_f=5, n_fit=20, i_max=i_max, stream=stream)
+                assert min(21, i_max + 1) <= n2 <= i_max + 1
+            ctx.close()
+        (n0, h0, s0, k0), (n1, h1, s1, k1) = res
+        assert n0 == n1 and k0 == k1, (n0, n1, k0, k1)
+        if i_max == 15:
+            assert n0 == 16  # no check before sweep n_fit = 20: the run stops at i_max
+        assert np.array_equal(h0, h1)
+        for a, b in zip(s0, s1):
+            assert np.array_equal(a, b)
 
 
 def _sweep_parity(model_kw, oracle_sweep, path, R=4, T=0.13, sweeps=3):
@@ -239,3 +274,49 @@ def test_mpr_beats_gmrf_on_lognormal_data():
             maes[model].append(float(np.mean(np.abs(zh[m] - z[m]))))
     print(maes)
     assert np.mean(maes["mpr"]) < np.mean(maes["gmrf"])
+
+
+def _cv_inputs(kind):
+    if kind == "grf64":
+        z, g = _grf64()
+    else:
+        z = synthetic.lognormal_grf((64, 64), nu=0.5, ell=8.0, log_mean=0.0, log_std=1.0, seed=31)
+        g = synthetic.uniform_gaps((64, 64), 0.33, 32)
+    hold = (synthetic.uniform_gaps(g.shape, 0.15, 4242) & (g == 0)).astype(np.uint8)
+    return z.astype(np.float32), g.astype(np.uint8), hold
+
+
+@pytest.mark.parametrize("kind", ["grf64", "lognormal64"])
+def test_select_q_matches_the_oracle(kind):
+    """Cross-validated q (mpr_select_q) against the oracle's procedure on the same
+    validation set: per candidate the SEM temperature within 1% and the validation
+    AAE within 2%; the GPU's choice scores, by the oracle's own scores, within 0.5% of
+    the oracle's best (on the Gaussian field the scores of all q lie within about
+    0.1% of each other, below the Monte Carlo noise, so the argmin itself is not
+    unique there), and on the lognormal field both choose q = 1/2."""
+    z, g, hold = _cv_inputs(kind)
+    qs = [0.1, 0.25, 0.5]
+    R, ne, nm = 16, 100, 100
+    got = mpr.select_q(z, g, hold, qs, chains=R, n_equil=ne, n_meas=nm,
+                       params=mpr.Params(seed=SEED),
+                       topts=mpr.TOpts(L=64, chains=16, n_equil=60, n_meas=120, iters=6))
+    ref = oracle.select_q(z.astype(np.float64), g, hold, qs, R=R, n_equil=ne, n_meas=nm,
+                          seed=SEED, sem=dict(L=64, K=4, n_eq=100, n_meas=150, rel_tol=2e-3))
+    print(kind, got, ref)
+    assert np.all(np.abs(got["T"] - ref["T"]) < 0.01 * ref["T"]), (got["T"], ref["T"])
+    assert np.all(np.abs(got["scores"] - ref["scores"]) < 0.02 * ref["scores"])
+    assert got["q"] == qs[int(np.argmin(got["scores"]))]
+    k_gpu = qs.index(got["q"])
+    assert ref["scores"][k_gpu] <= 1.005 * ref["scores"].min()
+    if kind == "lognormal64":
+        assert got["q"] == 0.5 and ref["q"] == 0.5
+
+
+def test_select_q_errors():
+    z, g, hold = _cv_inputs("grf64")
+    with pytest.raises(mpr._lib.MprError) as err:
+        mpr.select_q(z, g, np.zeros_like(hold), [0.5], chains=2, n_equil=2, n_meas=2)
+    assert err.value.status == 1
+    with pytest.raises(mpr._lib.MprError) as err:
+        mpr.select_q(z, g, hold, [0.6], chains=2, n_equil=2, n_meas=2)
+    assert err.value.status == 1

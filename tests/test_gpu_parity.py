@@ -7,6 +7,7 @@ except where a decision lay within tolerance of its threshold (Metropolis:
 1e-6), those counted and kept at or below 1e-4 of the sites.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -441,6 +442,53 @@ def test_long_run_statistics_and_prediction_grf64():
     assert abs(rmse_g - rmse_o) < 0.02 * rmse_o, (rmse_g, rmse_o)
     # sample pixels are returned unchanged
     assert np.array_equal(zh[~m], z[~m])
+
+
+def test_long_run_statistics_lognormal256(golden_dir):
+    """A 256 x 256 field shaped like the 1024 x 1024 lognormal workload (Matern
+    nu = 1.5, ell = 20, log-std 0.8, 50% gaps), 100 realisations: the SEM temperature
+    within 1% of the oracle's bisection, and at the oracle's T the mean specific
+    energy within 3 sigma and MAE / RMSE within 2% of the oracle's long run (the
+    oracle's figures from tests/golden/make_longrun_lognormal256.py)."""
+    import json
+    with open(os.path.join(golden_dir, "lognormal256_longrun.json")) as f:
+        ref = json.load(f)
+    w = synthetic.workload("lognormal1024", L=ref["input"]["side"])
+    z, g = w.z[0], w.gap[0]
+    sim = ref["simulate"]
+    R = sim["blocks"] * sim["chains_per_block"]
+    ne, nm = sim["n_equil"], sim["n_meas"]
+    sem = ref["sem"]
+    topts = mpr.TOpts(L=sem["L"], chains=16, n_equil=60, n_meas=120, iters=6)
+    ctx = mpr.Context([z], [g], chains=R, params=mpr.Params(seed=SEED + 7), topts=topts)
+    assert abs(ctx.image_info()["e_s"][0] - ref["e_s"]) < 1e-6
+    T_gpu = ctx.estimate_T()[0]
+    assert abs(T_gpu - sem["T"]) < 0.01 * sem["T"], (T_gpu, sem["T"])
+    ctx.set_T([sem["T"]])
+    ctx.sweep(ne, "equil")
+    es = []
+    for _ in range(nm):
+        ctx.sweep(1, "measure", record_energy=True)
+        es.append(ctx.chain_info()["e_last"][0])
+    m_g = np.array(es).mean(0)              # per-realisation means
+    m_o = np.array(ref["e_chain_mean"])
+    sig = math.sqrt(m_g.var(ddof=1) / len(m_g) + m_o.var(ddof=1) / len(m_o))
+    # at this T the chains' energies spread by a few 1e-7 only, the size of the FP32
+    # energy evaluation's own error: that error, measured on the final states (the
+    # recorded FP32 energy against the FP64 energy of the same angles), is allowed
+    # on top of 3 sigma
+    fin = ctx.get_state()[0].cpu().numpy().astype(np.float64)
+    e_fp64 = np.array([oracle.specific_energy(fin[c]) for c in range(R)])
+    bias = float(np.mean(np.array(es[-1]) - e_fp64))
+    assert abs(bias) < 2e-6
+    assert abs(m_g.mean() - m_o.mean()) < 3 * sig + abs(bias), (m_g.mean(), m_o.mean(), sig, bias)
+    zh = ctx.predict()[0].cpu().numpy().astype(np.float64)
+    m = g == 1
+    err = zh[m] - z[m].astype(np.float64)
+    mae, rmse = float(np.mean(np.abs(err))), float(np.sqrt(np.mean(err ** 2)))
+    assert abs(mae - ref["mae"]) < 0.02 * ref["mae"], (mae, ref["mae"])
+    assert abs(rmse - ref["rmse"]) < 0.02 * ref["rmse"], (rmse, ref["rmse"])
+    ctx.close()
 
 
 def test_estimate_T_newton_matches_oracle_bisection():

@@ -290,6 +290,27 @@ def test_high_temperature_limit():
     assert abs(m + 4 / math.pi**2) < 4e-3
 
 
+@pytest.mark.parametrize("q", [0.2, 0.35])
+def test_high_temperature_limit_general_q(q):
+    """At beta = 0, <cos(q dphi)> = |<exp(i q phi)>|^2 = (sin(pi q) / (pi q))^2 for i.i.d.
+    U(0, 2 pi) angles, the upper end of e(T) for any q."""
+    s = math.sin(math.pi * q) / (math.pi * q)
+    m, _ = oracle.e_of_T(1e8, L=16, K=4, n_eq=20, n_meas=300, seed=14, q=q)
+    assert abs(m + s * s) < 4e-3
+
+
+def test_estimate_T_range_follows_q():
+    """The SEM root exists only for e_s between -J and the q-dependent infinite-temperature
+    value: at q = 0.2 that is -0.8751, so an e_s between it and -4/pi^2 has no root."""
+    q = 0.2
+    s = math.sin(math.pi * q) / (math.pi * q)
+    e_inf = -s * s
+    with pytest.raises(ValueError):
+        oracle.estimate_T(0.5 * (e_inf - 4 / math.pi**2), L=8, K=1, n_eq=5, n_meas=5, seed=1, q=q)
+    T = oracle.estimate_T(e_inf - 0.02, L=16, K=2, n_eq=40, n_meas=40, seed=1, q=q)
+    assert 1e-3 < T < 10.0
+
+
 def test_low_temperature_slope():
     """Harmonic limit (derived, loose): e ~ -1 + T/4 for large L as T -> 0."""
     m, _ = oracle.e_of_T(0.01, L=32, K=2, n_eq=150, n_meas=100, seed=15)
@@ -644,3 +665,61 @@ def test_fill_reproduces_the_papers_validation_band(frac, maae, mrase):
         res = np.array(pool.map(_table2_fill, [(s, frac) for s in range(8)]))
     assert abs(res[:, 0].mean() - maae) < 0.05 * maae, res[:, 0].mean()
     assert abs(res[:, 1].mean() - mrase) < 0.05 * mrase, res[:, 1].mean()
+
+
+# ------------------------------------------- cross-validated q (conclusions)
+
+def _cv_case(outlier):
+    rng = np.random.default_rng(77)
+    z = rng.uniform(0.0, 10.0, size=(5, 5))
+    gap = np.zeros((5, 5), np.uint8)
+    gap[0, 4] = 1                      # one gap of the image itself
+    hold = np.zeros((5, 5), np.uint8)
+    for y, x in ((1, 1), (3, 1), (1, 3), (3, 3)):
+        hold[y, x] = 1                 # validation points: all four neighbours are samples
+    if outlier:
+        z[3, 3] = 1000.0               # a validation value far outside the training range
+    return z, gap, hold
+
+
+@pytest.mark.parametrize("outlier", [False, True])
+def test_select_q_scores_by_quadrature(outlier):
+    """Every validation point of the 5 x 5 case has four training samples as neighbours,
+    so given the samples the held-out angles are independent and each has the 1-D
+    conditional law exp((J/T) sum_j cos(q (phi - phi_j))) on [0, 2 pi).  At the T the
+    procedure inferred for each q, the score must equal the AAE of the back-transformed
+    quadrature means (angle map from the training samples' extremes alone) within the
+    Monte Carlo error, and the chosen q must be the first smallest score."""
+    z, gap, hold = _cv_case(outlier)
+    qs = [0.15, 0.3, 0.5]
+    R, ne, nm = 32, 100, 400
+    res = oracle.select_q(z, gap, hold, qs, R=R, n_equil=ne, n_meas=nm, seed=91,
+                          sem=dict(L=8, K=4, n_eq=100, n_meas=200))
+    train = (gap == 0) & (hold == 0)
+    zmin, zmax = z[train].min(), z[train].max()
+    scale = (zmax - zmin) / TWO_PI
+    phi = (z - zmin) / scale
+    pts = np.argwhere(hold == 1)
+    for q, T, score in zip(qs, res["T"], res["scores"]):
+        assert 0.0 < T < 20.0
+        errs, sds = [], []
+        for y, x in pts:
+            nb = [phi[y + dy, x + dx] for dy, dx in ((-1, 0), (1, 0), (0, -1), (0, 1))]
+
+            def dens(v, nb=nb, q=q, T=T):
+                return math.exp(sum(math.cos(q * (v - p)) - 1.0 for p in nb) / T)
+
+            Z = integrate.quad(dens, 0, TWO_PI, limit=400)[0]
+            m1 = integrate.quad(lambda v: v * dens(v), 0, TWO_PI, limit=400)[0] / Z
+            m2 = integrate.quad(lambda v: v * v * dens(v), 0, TWO_PI, limit=400)[0] / Z
+            errs.append(abs(zmin + scale * m1 - z[y, x]))
+            # standard error of the mean over R * nm correlated sweeps (x3 for correlation)
+            sds.append(scale * math.sqrt(max(m2 - m1 * m1, 0.0) * 3.0 / (R * nm)))
+        ref = float(np.mean(errs))
+        tol = 5.0 * float(np.mean(sds)) + 1e-9 * max(1.0, ref)
+        assert abs(score - ref) < tol, (q, T, score, ref, tol)
+    k = int(np.argmin(res["scores"]))
+    assert res["q"] == qs[k]
+    with pytest.raises(ValueError):
+        oracle.select_q(z, gap, np.zeros_like(hold), qs, R=2, n_equil=2, n_meas=2, seed=1,
+                        sem=dict(L=8, K=1, n_eq=5, n_meas=5))
