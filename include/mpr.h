@@ -145,7 +145,11 @@ mpr_status mpr_init_grid(mpr_ctx** out, int n_img, const int* Lx, const int* Ly,
  * given batch (after one warm-up sweep, temperature from the harmonic guess
  * 4 (e_s + J)) for each candidate tile shape (32x16, 16x16, 32x32) and chain
  * group (automatic, 16, 8) that fits `workspace`, and writes the fastest into
- * p->tile_x, tile_y, chain_group.  timings (nullable, host [9]) receives
+ * p->tile_x, tile_y, chain_group.  The chain group also sets the sites per
+ * thread: a lane takes one chain pair of a site, so a warp step covers
+ * 64 / group sites and a thread updates about (own-colour gap sites of the
+ * tile) x group / (2 x threads per block) sites per launch (6.4, 3.2 and 1.6
+ * for groups of 32, 16 and 8 on 16x16 tiles with 40% gaps).  timings (nullable, host [9]) receives
  * milliseconds per sweep, tile-major, -1 for skipped candidates.  The
  * workspace is scratch here (size it with mpr_workspace_size for 16x16
  * tiles, the largest layout).  Blocking; the batch itself is not changed. */

@@ -118,7 +118,6 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     // the tile record carries everything the addresses need (one dependent load)
     const TileDesc T = a.tiles[tile];
     const int c = a.colour;
-    const int oc = c ^ 1;
     const int n_own = c ? T.cnt[1] : T.cnt[0];
     const bool energy = (a.flags & kEnergy) != 0;
     const int n_oth = c ? T.cnt[0] : T.cnt[1];
