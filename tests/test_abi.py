@@ -72,6 +72,26 @@ def test_host_only_calls(lib):
     # NULL inputs are rejected before any device work
     assert lib.mpr_init_grid(C.byref(out), 2, Lx, Ly, 4, C.byref(p), None, None, None, 0, None, 0,
                              None) == 1
+    # cross-validated q: workspace sizing and argument checks, all before any device work
+    qb = C.c_size_t()
+    assert lib.mpr_select_q_workspace_size(64, 64, 8, C.byref(p), None, C.byref(qb)) == 0
+    assert lib.mpr_workspace_size(1, _lib.int_array([64]), _lib.int_array([64]), None, 8,
+                                  C.byref(p), None, C.byref(nbytes)) == 0
+    assert qb.value > nbytes.value  # one context plus the staged inputs
+    dummy = C.c_void_p(256)          # never dereferenced: the checks below fail first
+    qs = (C.c_double * 2)(0.25, 0.6)
+    sc = (C.c_double * 2)()
+    assert lib.mpr_select_q(64, 64, dummy, dummy, dummy, 0, 2, qs, 8, 10, 10, C.byref(p), None,
+                            dummy, qb, sc, None, None, None) == 1
+    assert b"(0, 1/2]" in lib.mpr_last_error()
+    qs[1] = 0.5
+    assert lib.mpr_select_q(64, 64, dummy, dummy, dummy, 0, 2, qs, 8, 10, 0, C.byref(p), None,
+                            dummy, qb, sc, None, None, None) == 1
+    p.model = 1
+    assert lib.mpr_select_q(64, 64, dummy, dummy, dummy, 0, 2, qs, 8, 10, 10, C.byref(p), None,
+                            dummy, qb, sc, None, None, None) == 1
+    assert b"MPR bond" in lib.mpr_last_error()
+    p.model = 0
 
 
 def test_no_cpu_fallback_in_product_package():
