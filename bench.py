@@ -71,7 +71,8 @@ def recorded_traffic_per_update():
 
 def record_traffic(csv_path, size, command):
     """Writes the traffic record from `ncu --page raw --csv` output of one sampling
-    launch of the colour pass (the kernel whose name carries the accumulate flag 1)
+    launch of the colour pass (the kernel whose accumulation mode, its fifth
+    template argument, is not 0)
     on the benchmark field at side `size`: DRAM bytes read + written per gap
     site-update, and the kernel sources' hash at the time of writing."""
     import csv
@@ -80,7 +81,9 @@ def record_traffic(csv_path, size, command):
         rows = list(csv.reader(l for l in f if not l.startswith("==")))
     head, units = rows[0], rows[1]
     k = head.index("Kernel Name")
-    hit = [r for r in rows[2:] if "tiled_pass_kernel<" in r[k] and ", 1, " in r[k]]
+    import re
+    pat = re.compile(r"tiled_pass_kernel<\d+, \d+, \d+, \d+, ([12]), \d+>")
+    hit = [r for r in rows[2:] if pat.search(r[k])]
     if not hit:
         raise SystemExit("no sampling launch of the colour pass in " + csv_path)
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
@@ -291,6 +294,7 @@ def run_gpu(args):
 
     sweep_events = []
     equil_events = []
+    launches = []
 
     def step(z_in, g_in, host_out=None, timed=False):
         ctx = mpr.Context([z_in], [g_in], chains=R, params=params, topts=topts, device=dev)
@@ -304,6 +308,8 @@ def run_gpu(args):
             q0 = torch.cuda.Event(enable_timing=True)
             q1 = torch.cuda.Event(enable_timing=True)
             q0.record(stream)
+        if not launches:
+            launches.extend(ctx.sweep_launches())
         ctx.sweep(ne, "equil")
         if timed:
             q1.record(stream)
@@ -400,13 +406,13 @@ def run_gpu(args):
                 "d2h_bytes_per_step": N * 4},
         "clocks": clocks,
     }
-    # kernel launches of one step: 3 per sweep (two colour passes + bookkeeping) for the
-    # main chains and for the temperature lattices, plus the fixed init/predict kernels
+    # kernel launches of one step: the library's per-sweep count for the realisations
+    # and for the temperature lattices, the Newton steps (and their set-up), the 16
+    # initialisation kernels of the two contexts (map, extremes, sample energy, tile
+    # tables, hot starts, chain set-up) and the prediction
     t_sweeps = topts.iters * (topts.n_equil + topts.n_meas) + topts.n_equil
-    # per step: 3 launches per sweep (two colour passes + bookkeeping) for the
-    # realisations and for the temperature lattices, the Newton steps and the
-    # init / predict kernels of both contexts
-    line["gpu_launches"] = args.steps * (3 * (ne + nm) + 3 * t_sweeps + topts.iters + 1 + 16)
+    line["gpu_launches"] = args.steps * (launches[0] * (ne + nm) + launches[1] * t_sweeps
+                                         + topts.iters + 1 + 16 + 1)
     if not args.no_plain:
         # the plain single-image path on the same job (one warm-up, one timed step)
         plain = mpr.Params(seed=12345 + rank, path="plain")

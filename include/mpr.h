@@ -230,6 +230,15 @@ mpr_status mpr_select_q(int Lx, int Ly, const float* z, const uint8_t* gap, cons
                         size_t ws_bytes, double* scores, double* T_out, double* q_best,
                         mpr_stream stream);
 
+/* Kernel launches one sweep of the context issues (per_sweep) and one sweep of
+ * its temperature lattices (per_T_sweep, nullable; 0 without lattices): per
+ * colour pass one launch for the tiles whose tables fit the blocks per SM the
+ * threads allow, one for the rest when there are any, one for the chains left
+ * over by the chain groups when there are any, and one bookkeeping launch per
+ * sweep (the plain path: two passes and the bookkeeping).  A graph replay of n
+ * sweeps runs n times that many kernels.  Host only. */
+mpr_status mpr_sweep_launches(const mpr_ctx* ctx, int* per_sweep, int* per_T_sweep);
+
 /* Sets / reads the reduced temperature of every image (host [n_img]). */
 mpr_status mpr_set_T(mpr_ctx* ctx, const double* T, mpr_stream stream);
 mpr_status mpr_get_T(mpr_ctx* ctx, double* T, mpr_stream stream);

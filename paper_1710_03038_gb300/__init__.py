@@ -22,7 +22,8 @@ from . import _lib
 from ._lib import MprParams, MprTOpts, call, int_array, i64_array
 
 __all__ = ["Params", "TOpts", "Context", "fill", "MPREnergy", "lattice_energy", "lattice_torque",
-           "lattice_grad", "philox", "version", "workspace_size"]
+           "lattice_grad", "philox", "version", "workspace_size", "eT_table", "select_q",
+           "autotune", "sample_energy_noalloc"]
 
 
 def version() -> str:
@@ -333,6 +334,12 @@ class Context:
         s, e = C.c_uint32(), C.c_uint32()
         call("mpr_get_sweep_index", self._ctx, C.byref(s), C.byref(e))
         return s.value, e.value
+
+    def sweep_launches(self):
+        """Kernel launches per sweep of the realisations and of the temperature lattices."""
+        m, t = C.c_int(), C.c_int()
+        call("mpr_sweep_launches", self._ctx, C.byref(m), C.byref(t))
+        return m.value, t.value
 
     def set_sweep_index(self, sweep: int, equil_index: int, stream=None):
         call("mpr_set_sweep_index", self._ctx, C.c_uint32(sweep), C.c_uint32(equil_index),

@@ -36,7 +36,7 @@ EXPORTS = (
     "mpr_sample_energy_noalloc", "mpr_equilibrate", "mpr_get_energy_history",
     "mpr_get_accumulators", "mpr_set_accumulators",
     "mpr_eT_table_workspace_size", "mpr_eT_table", "mpr_set_T_from_table", "mpr_autotune",
-    "mpr_select_q_workspace_size", "mpr_select_q",
+    "mpr_select_q_workspace_size", "mpr_select_q", "mpr_sweep_launches",
 )
 
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
             "mpr_autotune": (i, [i, ip, ip, i, pp, vp, vp, i, vp, sz, i, dp, vp]),
             "mpr_sample_energy_noalloc": (i, [i, ip, ip, vp, vp, d, d, vp, vp, vp, vp, vp]),
             "mpr_select_q_workspace_size": (i, [i, i, i, pp, tp, C.POINTER(sz)]),
+            "mpr_sweep_launches": (i, [vp, ip, ip]),
             "mpr_select_q": (i, [i, i, vp, vp, vp, i, i, dp, i, i, i, pp, tp, vp, sz, dp, dp, dp,
                                  vp]),
         }

@@ -1188,6 +1188,21 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
     return MPR_OK;
 }
 
+// Kernel launches of one sweep, as launch_sweeps issues them: per colour the
+// light tiles (when any), the heavy tiles (when any) and the remaining chains
+// (when the chain count is not a multiple of the group), then the bookkeeping.
+int sweep_launch_count(const mpr_ctx* c) {
+    if (c->g.path != MPR_PATH_TILED) return 3;
+    ChainRange cr[2];
+    const int n_cr = chain_ranges(c, cr);
+    int n = 1;
+    for (int colour = 0; colour < 2; ++colour) {
+        const int nt = c->g.n_tiles, nl = c->n_light[colour];
+        n += (nl > 0 ? 1 : 0) + (nl < nt ? 1 : 0) + (n_cr > 1 ? 1 : 0);
+    }
+    return n;
+}
+
 // Launch settings that may not change during a stream capture (the colour
 // passes' shared-memory attributes) are applied before one begins.
 mpr_status prepare_capture(mpr_ctx* c, cudaStream_t s) {
@@ -1686,6 +1701,13 @@ mpr_status mpr_equilibrate(mpr_ctx* c, int n_f, int n_fit, int i_max, int* n_don
     }
     if (n_done) *n_done = done;
     return check_device_status(c, s);
+}
+
+mpr_status mpr_sweep_launches(const mpr_ctx* c, int* per_sweep, int* per_T_sweep) {
+    if (!c || !per_sweep) return fail(MPR_ERR_INVALID_ARG, "NULL argument");
+    *per_sweep = sweep_launch_count(c);
+    if (per_T_sweep) *per_T_sweep = c->sub ? sweep_launch_count(c->sub) : 0;
+    return MPR_OK;
 }
 
 mpr_status mpr_get_energy_history(mpr_ctx* c, double* out, mpr_stream stream) {

@@ -27,9 +27,11 @@
 //  - updates every own-colour gap site of every chain with Alg. 1, one Philox
 //    block and one packed FP32x2 instruction stream serving the site in both
 //    chains of a pair, and stores the new pair as one float2;
-//  - in sampling sweeps, once every site is done, reads the new angles back
-//    from L2 one site per thread and adds their sum (and sum of squares) over
-//    the chain group to the FP64 realisation sums.
+//  - in sampling sweeps adds each site's sum (and sum of squares) over the
+//    chain group to the FP64 realisation sums: when one block covers every
+//    chain of the tile, a warp reads its sites' new rows back from L2 once its
+//    updates are done, one site per lane; with several chain groups per tile a
+//    shuffle butterfly over the lanes of a site forms the sums in the loop.
 // Acceptances and energies stay in registers until the end of the block.
 //
 // Energy (black pass).  Every bond joins a red and a black site.  H is the
@@ -52,6 +54,11 @@ namespace mpr {
 namespace tiled {
 
 enum Model : int { kModelMPR = 0, kModelLIT = 1, kModelGMRF = 2 };
+
+// How a pass treats the realisation sums: none (equilibration), read the new
+// rows back after the update loop (one chain group per tile), or form them in
+// the loop with a shuffle butterfly over the lanes of a site (several groups).
+enum AccMode : int { kAccNone = 0, kAccReadBack = 1, kAccButterfly = 2 };
 
 // bytes of one (entry, pair) table cell
 template <int MODEL>
@@ -94,7 +101,7 @@ __device__ __forceinline__ float2 gmrf_bond2(float2 phi, float v) {
     return fma2(mul2(d, d), f2(0.050660591821168885f), f2(-1.0f));
 }
 
-template <int TX, int TY, int NW, int P, bool ACC, int MODEL>
+template <int TX, int TY, int NW, int P, int ACC, int MODEL>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))  // 64 registers: 32 warps per SM
 tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     using Cf = Cfg<TX, TY, NW, MODEL>;
@@ -330,12 +337,32 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         const bool act1 = act && has1;
         // a missing second chain is the padding chain of the layout: storing there is harmless
         if (act) *reinterpret_cast<float2*>(sto + j * cpi) = o.phi;
+        if (ACC == kAccButterfly) {
+            // the site's sums over this block's chains: the lane's pair gives
+            // a = phi_0 + phi_1 and b = phi_0^2 + phi_1^2; a transposed butterfly over
+            // the P lanes of the site leaves sum a in lane p = 0 and sum b in p = P/2
+            const float x0 = act ? o.phi.x : 0.0f, x1 = act1 ? o.phi.y : 0.0f;
+            const float av = x0 + x1;
+            const float bv = fmaf(x0, x0, x1 * x1);
+            float keep = av;
+            if (P > 1) {
+                const bool up = (p & (P / 2)) != 0;
+                keep = (up ? bv : av) + __shfl_xor_sync(0xffffffffu, up ? av : bv, P / 2);
+#pragma unroll
+                for (int m = P / 4; m >= 1; m >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, m);
+            }
+            if (in) {
+                if (p == 0) atomicAdd(a.acc1 + slot_off + off_own + j, (double)keep);
+                if ((a.flags & kAccumulate2) && p == (P > 1 ? P / 2 : 0))
+                    atomicAdd(a.acc2 + slot_off + off_own + j, (double)(P > 1 ? keep : bv));
+            }
+        }
         cnt0 += (act && o.acc0) ? 1u : 0u;
         cnt1 += (act1 && o.acc1) ? 1u : 0u;
         if (energy) esum = add2(esum, make_float2(act ? o.e.x : 0.0f, act1 ? o.e.y : 0.0f));
     }
 
-    if (ACC) {
+    if (ACC == kAccReadBack) {
         // realisation sums of the sites this warp updated: their rows are read
         // back (from L2, past L1) one site per lane, ordered after the warp's
         // stores by the warp barrier, and added to the FP64 sums with
@@ -410,7 +437,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     }
 }
 
-template <int TX, int TY, int NW, int P, bool ACC, int MODEL>
+template <int TX, int TY, int NW, int P, int ACC, int MODEL>
 cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, bool setup_only) {
     using Cf = Cfg<TX, TY, NW, MODEL>;
     static_assert(Cf::smem_max <= 227 * 1024, "shared memory");
@@ -432,11 +459,17 @@ cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, bool setup_only) {
 template <int TX, int TY, int NW, int P, int MODEL>
 cudaError_t launch_cfg(const SweepArgs& a, cudaStream_t s, bool setup_only) {
     if (setup_only) {
-        cudaError_t e = launch_one<TX, TY, NW, P, false, MODEL>(a, s, true);
-        return e != cudaSuccess ? e : launch_one<TX, TY, NW, P, true, MODEL>(a, s, true);
+        cudaError_t e = launch_one<TX, TY, NW, P, kAccNone, MODEL>(a, s, true);
+        if (e == cudaSuccess) e = launch_one<TX, TY, NW, P, kAccReadBack, MODEL>(a, s, true);
+        return e != cudaSuccess ? e : launch_one<TX, TY, NW, P, kAccButterfly, MODEL>(a, s, true);
     }
-    if (a.flags & kAccumulate) return launch_one<TX, TY, NW, P, true, MODEL>(a, s, false);
-    return launch_one<TX, TY, NW, P, false, MODEL>(a, s, false);
+    if (!(a.flags & kAccumulate)) return launch_one<TX, TY, NW, P, kAccNone, MODEL>(a, s, false);
+    // sampling sweeps: with one block covering every chain of a tile the new rows
+    // are read back after the update loop; with several chain groups per tile the
+    // sums are formed in the loop (measured faster there)
+    const bool one_group = a.chain0 == 0 && a.chain_end == a.n_chains && a.chain_group >= a.n_chains;
+    if (one_group) return launch_one<TX, TY, NW, P, kAccReadBack, MODEL>(a, s, false);
+    return launch_one<TX, TY, NW, P, kAccButterfly, MODEL>(a, s, false);
 }
 
 // pairs per site for a chain group of cg chains: the next power of two of
