@@ -159,18 +159,18 @@ def test_sweep_by_sweep_parity_ragged_batch(path):
     print(tally)
 
 
-@pytest.mark.parametrize("path", ["tiled", "plain"])
+@pytest.mark.parametrize("path,R,cg", [("tiled", 4, 0), ("plain", 4, 0), ("tiled", 8, 4)])
 @pytest.mark.parametrize("freeze_a", [True, False])
-def test_measurement_sweeps_match_oracle_state_by_state(path, freeze_a):
+def test_measurement_sweeps_match_oracle_state_by_state(path, R, cg, freeze_a):
     """Alg. 2 step 5 from a shared state: three sampling sweeps, each against the
     oracle's sweep with the a that step 5.2 prescribes (the frozen equilibration a,
     or a = 1 as printed); a and the equilibration index stay put; the realisation
     sums equal the sums of the GPU's own states (FP32 partial sums) and the oracle's
     states wherever no decision flipped; the prediction and its spread follow from
-    the sums."""
+    the sums.  With 8 chains in groups of 4 the tiled pass forms the sums in its
+    update loop (several groups per tile), otherwise it reads the rows back."""
     zs, gs = ragged_images()
-    R = 4
-    ctx = make_ctx(zs, gs, R, path, freeze_a_in_measure=freeze_a)
+    ctx = make_ctx(zs, gs, R, path, freeze_a_in_measure=freeze_a, chain_group=cg)
     T = np.array([0.15, 0.3, 0.08, 0.5])
     ctx.set_T(T)
     ctx.sweep(4, "equil")
@@ -567,3 +567,35 @@ def test_degenerate_shapes_sweep_parity(path):
         p = p.cpu().numpy()
         assert np.array_equal(p[g == 0], z[g == 0])
         assert np.all(np.isfinite(p))
+
+
+@pytest.mark.parametrize("path", ["tiled", "plain"])
+def test_longest_sides_sweep_parity(path):
+    """Images at the longest side the layout allows (65535: the random stream's
+    counter keeps y in 16 bits and x >> 1 in 16), as 2-row and 2-column strips:
+    two sweeps against the oracle under the decision-parity rule."""
+    shapes = [(2, 65535), (65535, 2)]
+    zs, gs = [], []
+    for k, (h, w) in enumerate(shapes):
+        rng = np.random.default_rng(70 + k)
+        zs.append((50 + 10 * np.cumsum(rng.standard_normal(h * w)) / 100).reshape(h, w).astype(np.float32))
+        gs.append(synthetic.uniform_gaps((h, w), 0.4, 80 + k).astype(np.uint8))
+    R = 2
+    ctx = make_ctx(zs, gs, R, path)
+    T = np.array([0.2, 0.3])
+    ctx.set_T(T)
+    n_main, n_T = ctx.sweep_launches()
+    assert n_main >= 3 and n_T >= 3
+    tally = Tally()
+    for _ in range(2):
+        before = [s.cpu().numpy() for s in ctx.get_state()]
+        a = ctx.chain_info()["a"]
+        s_idx, _ = ctx.sweep_index()
+        ctx.sweep(1, "equil")
+        after = [s.cpu().numpy() for s in ctx.get_state()]
+        for i, g in enumerate(gs):
+            for c in range(R):
+                compare_sweep(before[i][c], after[i][c], g, tally, T=T[i], a=a[i, c], seed=SEED,
+                              img=i, chain=c, sweep_index=s_idx)
+    tally.assert_budget()
+    print(tally)
