@@ -27,11 +27,10 @@
 //  - updates every own-colour gap site of every chain with Alg. 1, one Philox
 //    block and one packed FP32x2 instruction stream serving the site in both
 //    chains of a pair, and stores the new pair as one float2;
-//  - in sampling sweeps adds each site's sum (and sum of squares) over the
-//    chain group to the FP64 realisation sums: when one block covers every
-//    chain of the tile, a warp reads its sites' new rows back from L2 once its
-//    updates are done, one site per lane; with several chain groups per tile a
-//    shuffle butterfly over the lanes of a site forms the sums in the loop.
+//  - in sampling sweeps sums each site's new angles (and their squares) over
+//    the chain group in shared memory, in fixed point (2^-24 rad, 2^-21 rad^2:
+//    integer adds, exact and independent of their order), and adds the sums
+//    to the FP64 realisation sums once every site is done.
 // Acceptances and energies stay in registers until the end of the block.
 //
 // Energy (black pass).  Every bond joins a red and a black site.  H is the
@@ -55,10 +54,6 @@ namespace tiled {
 
 enum Model : int { kModelMPR = 0, kModelLIT = 1, kModelGMRF = 2 };
 
-// How a pass treats the realisation sums: none (equilibration), read the new
-// rows back after the update loop (one chain group per tile), or form them in
-// the loop with a shuffle butterfly over the lanes of a site (several groups).
-enum AccMode : int { kAccNone = 0, kAccReadBack = 1, kAccButterfly = 2 };
 
 // bytes of one (entry, pair) table cell
 template <int MODEL>
@@ -81,7 +76,11 @@ struct Cfg {
     static constexpr size_t off_f1 = off_k + sizeof(uint4) * NMAX;
     static constexpr size_t off_red = off_f1 + (MODEL == kModelLIT ? sizeof(float4) * NMAX : 0);
     // the table last, sized at launch for the largest tile of the pass
-    static constexpr size_t off_tab = off_red + sizeof(float4) * NW * 16;
+    // the per-chain reduction area; sampling passes first keep the own sites'
+    // fixed-point realisation sums there (two words per site)
+    static constexpr size_t red_bytes =
+        sizeof(float4) * NW * 16 > 8 * NMAX ? sizeof(float4) * NW * 16 : 8 * NMAX;
+    static constexpr size_t off_tab = off_red + red_bytes;
     static constexpr size_t smem_for(int gt, int P) {
         return off_tab + (size_t)Cell<MODEL>::bytes * P * gt;
     }
@@ -101,7 +100,7 @@ __device__ __forceinline__ float2 gmrf_bond2(float2 phi, float v) {
     return fma2(mul2(d, d), f2(0.050660591821168885f), f2(-1.0f));
 }
 
-template <int TX, int TY, int NW, int P, int ACC, int MODEL>
+template <int TX, int TY, int NW, int P, bool ACC, int MODEL>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))  // 64 registers: 32 warps per SM
 tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     using Cf = Cfg<TX, TY, NW, MODEL>;
@@ -115,6 +114,10 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     float4* own_f1 = reinterpret_cast<float4*>(smem + Cf::off_f1);
     float4* red = reinterpret_cast<float4*>(smem + Cf::off_red);
     unsigned char* tab = smem + Cf::off_tab;
+    // sampling passes: per own site, the sums over the block's chains of phi
+    // (units of 2^-24 rad) and of phi^2 (units of 2^-21 rad^2), exact in 32 bits
+    // for up to 32 chains
+    uint32_t* accs = reinterpret_cast<uint32_t*>(smem + Cf::off_red);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -186,6 +189,8 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     {
         const long long b = slot_off + off_own;
         constexpr uint32_t kRow = (uint32_t)CB * P;  // bytes per table entry
+        if (ACC)
+            for (int j = tid; j < n_own; j += NT) accs[j] = accs[Cf::NMAX + j] = 0u;
         for (int j = tid; j < n_own; j += NT) {
             const uint2 r = a.slot_ref[b + j];
             const float4 f = a.slot_cs[b + j];
@@ -337,70 +342,28 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         const bool act1 = act && has1;
         // a missing second chain is the padding chain of the layout: storing there is harmless
         if (act) *reinterpret_cast<float2*>(sto + j * cpi) = o.phi;
-        if (ACC == kAccButterfly) {
-            // the site's sums over this block's chains: the lane's pair gives
-            // a = phi_0 + phi_1 and b = phi_0^2 + phi_1^2; a transposed butterfly over
-            // the P lanes of the site leaves sum a in lane p = 0 and sum b in p = P/2
-            const float x0 = act ? o.phi.x : 0.0f, x1 = act1 ? o.phi.y : 0.0f;
-            const float av = x0 + x1;
-            const float bv = fmaf(x0, x0, x1 * x1);
-            float keep = av;
-            if (P > 1) {
-                const bool up = (p & (P / 2)) != 0;
-                keep = (up ? bv : av) + __shfl_xor_sync(0xffffffffu, up ? av : bv, P / 2);
-#pragma unroll
-                for (int m = P / 4; m >= 1; m >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, m);
-            }
-            if (in) {
-                if (p == 0) atomicAdd(a.acc1 + slot_off + off_own + j, (double)keep);
-                if ((a.flags & kAccumulate2) && p == (P > 1 ? P / 2 : 0))
-                    atomicAdd(a.acc2 + slot_off + off_own + j, (double)(P > 1 ? keep : bv));
-            }
+        if (ACC && act) {
+            // this pair's part of the site's realisation sums, in fixed point
+            const float x0 = o.phi.x, x1 = act1 ? o.phi.y : 0.0f;
+            atomicAdd(&accs[j], __float2uint_rn((x0 + x1) * 16777216.0f));
+            atomicAdd(&accs[Cf::NMAX + j], __float2uint_rn(fmaf(x0, x0, x1 * x1) * 2097152.0f));
         }
         cnt0 += (act && o.acc0) ? 1u : 0u;
         cnt1 += (act1 && o.acc1) ? 1u : 0u;
         if (energy) esum = add2(esum, make_float2(act ? o.e.x : 0.0f, act1 ? o.e.y : 0.0f));
     }
 
-    if (ACC == kAccReadBack) {
-        // realisation sums of the sites this warp updated: their rows are read
-        // back (from L2, past L1) one site per lane, ordered after the warp's
-        // stores by the warp barrier, and added to the FP64 sums with
-        // fire-and-forget adds (one chain group per tile: one add per address)
-        __syncwarp();
+    if (ACC) {
+        // the block's sums go to the FP64 realisation sums (fire-and-forget adds;
+        // one add per site and block)
+        __syncthreads();
         const bool accum2 = (a.flags & kAccumulate2) != 0;
-        double* acc1 = a.acc1 + slot_off + off_own;
-        double* acc2 = a.acc2 + slot_off + off_own;
-        const float* base = a.state + T.state_off + (long long)off_own * cp + r0;
-        const bool vec4 = ((cp | r0 | ng) & 3) == 0;  // 16-byte aligned runs of 4 chains
-        const int n_mine = warp < n_steps ? ((n_steps - 1 - warp) / NW + 1) * SPW : 0;
-        for (int k = lane; k < n_mine; k += 32) {
-            const int j = (warp + (k / SPW) * NW) * SPW + (k % SPW);
-            if (j >= n_own) continue;
-            const float* src = base + (long long)j * cp;
-            float2 s1 = f2(0.0f), s2 = f2(0.0f);
-            if (vec4) {
-                for (int q = 0; q < ng; q += 4) {
-                    const float4 v = __ldcg(reinterpret_cast<const float4*>(src + q));
-                    const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
-                    s1 = add2(s1, add2(lo, hi));
-                    s2 = fma2(lo, lo, fma2(hi, hi, s2));
-                }
-            } else {
-                for (int q = 0; q + 1 < ng; q += 2) {
-                    const float2 v = __ldcg(reinterpret_cast<const float2*>(src + q));
-                    s1 = add2(s1, v);
-                    s2 = fma2(v, v, s2);
-                }
-                if (ng & 1) {
-                    const float v = __ldcg(src + ng - 1);
-                    s1.x += v;
-                    s2.x = fmaf(v, v, s2.x);
-                }
-            }
-            atomicAdd(acc1 + j, (double)(s1.x + s1.y));
-            if (accum2) atomicAdd(acc2 + j, (double)(s2.x + s2.y));
+        for (int j = tid; j < n_own; j += NT) {
+            atomicAdd(a.acc1 + slot_off + off_own + j, (double)accs[j] * 0x1p-24);
+            if (accum2)
+                atomicAdd(a.acc2 + slot_off + off_own + j, (double)accs[Cf::NMAX + j] * 0x1p-21);
         }
+        __syncthreads();  // the per-chain reduction below reuses the area
     }
 
     // -- per-chain totals: lanes of one pair, then warps ------------------------
@@ -437,7 +400,7 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
     }
 }
 
-template <int TX, int TY, int NW, int P, int ACC, int MODEL>
+template <int TX, int TY, int NW, int P, bool ACC, int MODEL>
 cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, bool setup_only) {
     using Cf = Cfg<TX, TY, NW, MODEL>;
     static_assert(Cf::smem_max <= 227 * 1024, "shared memory");
@@ -459,17 +422,11 @@ cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, bool setup_only) {
 template <int TX, int TY, int NW, int P, int MODEL>
 cudaError_t launch_cfg(const SweepArgs& a, cudaStream_t s, bool setup_only) {
     if (setup_only) {
-        cudaError_t e = launch_one<TX, TY, NW, P, kAccNone, MODEL>(a, s, true);
-        if (e == cudaSuccess) e = launch_one<TX, TY, NW, P, kAccReadBack, MODEL>(a, s, true);
-        return e != cudaSuccess ? e : launch_one<TX, TY, NW, P, kAccButterfly, MODEL>(a, s, true);
+        cudaError_t e = launch_one<TX, TY, NW, P, false, MODEL>(a, s, true);
+        return e != cudaSuccess ? e : launch_one<TX, TY, NW, P, true, MODEL>(a, s, true);
     }
-    if (!(a.flags & kAccumulate)) return launch_one<TX, TY, NW, P, kAccNone, MODEL>(a, s, false);
-    // sampling sweeps: with one block covering every chain of a tile the new rows
-    // are read back after the update loop; with several chain groups per tile the
-    // sums are formed in the loop (measured faster there)
-    const bool one_group = a.chain0 == 0 && a.chain_end == a.n_chains && a.chain_group >= a.n_chains;
-    if (one_group) return launch_one<TX, TY, NW, P, kAccReadBack, MODEL>(a, s, false);
-    return launch_one<TX, TY, NW, P, kAccButterfly, MODEL>(a, s, false);
+    if (a.flags & kAccumulate) return launch_one<TX, TY, NW, P, true, MODEL>(a, s, false);
+    return launch_one<TX, TY, NW, P, false, MODEL>(a, s, false);
 }
 
 // pairs per site for a chain group of cg chains: the next power of two of
