@@ -167,8 +167,8 @@ def test_measurement_sweeps_match_oracle_state_by_state(path, R, cg, freeze_a):
     or a = 1 as printed); a and the equilibration index stay put; the realisation
     sums equal the sums of the GPU's own states (FP32 partial sums) and the oracle's
     states wherever no decision flipped; the prediction and its spread follow from
-    the sums.  With 8 chains in groups of 4 the tiled pass forms the sums in its
-    update loop (several groups per tile), otherwise it reads the rows back."""
+    the sums.  With 8 chains in groups of 4 two blocks of the tiled pass add to
+    each site's sums."""
     zs, gs = ragged_images()
     ctx = make_ctx(zs, gs, R, path, freeze_a_in_measure=freeze_a, chain_group=cg)
     T = np.array([0.15, 0.3, 0.08, 0.5])
