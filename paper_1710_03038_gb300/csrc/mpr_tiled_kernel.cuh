@@ -29,8 +29,9 @@
 //    chains of a pair, and stores the new pair as one float2;
 //  - in sampling sweeps sums each site's new angles (and their squares) over
 //    the chain group in shared memory, in fixed point (2^-24 rad, 2^-21 rad^2:
-//    integer adds, exact and independent of their order), and adds the sums
-//    to the FP64 realisation sums once every site is done.
+//    integer adds, exact and independent of their order; lanes p and p + 8
+//    pre-add with one shuffle), and adds the sums to the FP64 realisation sums
+//    once every site is done.
 // Acceptances and energies stay in registers until the end of the block.
 //
 // Energy (black pass).  Every bond joins a red and a black site.  H is the
@@ -342,11 +343,21 @@ tiled_pass_kernel(const __grid_constant__ SweepArgs a) {
         const bool act1 = act && has1;
         // a missing second chain is the padding chain of the layout: storing there is harmless
         if (act) *reinterpret_cast<float2*>(sto + j * cpi) = o.phi;
-        if (ACC && act) {
-            // this pair's part of the site's realisation sums, in fixed point
-            const float x0 = o.phi.x, x1 = act1 ? o.phi.y : 0.0f;
-            atomicAdd(&accs[j], __float2uint_rn((x0 + x1) * 16777216.0f));
-            atomicAdd(&accs[Cf::NMAX + j], __float2uint_rn(fmaf(x0, x0, x1 * x1) * 2097152.0f));
+        if (ACC) {
+            // this pair's part of the site's realisation sums, added to that of
+            // pair p + 8 first (half the lanes on each shared-memory word), then
+            // in fixed point
+            const float x0 = act ? o.phi.x : 0.0f, x1 = act1 ? o.phi.y : 0.0f;
+            float sa = x0 + x1, sb = fmaf(x0, x0, x1 * x1);
+            constexpr int kAdders = P >= 16 ? 8 : P;
+            if (P >= 16) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, 8);
+                sb += __shfl_xor_sync(0xffffffffu, sb, 8);
+            }
+            if (in && p < kAdders) {
+                atomicAdd(&accs[j], __float2uint_rn(sa * 16777216.0f));
+                atomicAdd(&accs[Cf::NMAX + j], __float2uint_rn(sb * 2097152.0f));
+            }
         }
         cnt0 += (act && o.acc0) ? 1u : 0u;
         cnt1 += (act1 && o.acc1) ? 1u : 0u;
