@@ -44,3 +44,28 @@ def test_committed_record_when_present_is_plausible():
     # realisation sums' share, and far above zero
     assert 6.0 < float(rec["dram_bytes_per_gap_update"]) < 20.0
     assert len(rec["kernel_sources_sha16"]) == 16
+
+
+def test_record_is_written_from_an_ncu_raw_page(monkeypatch, tmp_path):
+    """`bench.py --record-traffic` takes the DRAM bytes of the sampling launch (the
+    colour pass whose accumulation argument is 1) from `ncu --page raw --csv` output
+    and divides by the gap site-updates of one launch on the field of that side."""
+    import csv
+    import synthetic
+    raw = tmp_path / "raw.csv"
+    with open(raw, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(["ID", "Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum"])
+        w.writerow(["", "", "Mbyte", "Kbyte"])
+        w.writerow(["0", "void tiled_pass_kernel<16, 16, 4, 16, 0, 0>(SweepArgs)", "9.0", "9.0"])
+        w.writerow(["1", "void tiled_pass_kernel<16, 16, 4, 16, 1, 0>(SweepArgs)", "2.0", "500.0"])
+    rec = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(rec))
+    bench.record_traffic(str(raw), 64, "ncu ...")
+    wl = synthetic.workload("lognormal4096", L=64)
+    updates = int(wl.gap[0].sum()) * wl.chains / 2.0
+    with open(rec) as f:
+        got = json.load(f)
+    assert got["dram_bytes_per_gap_update"] == round(2.5e6 / updates, 4)
+    assert got["kernel_sources_sha16"] == bench.kernel_sources_hash()
+    assert bench.recorded_traffic_per_update() == got["dram_bytes_per_gap_update"]
