@@ -57,16 +57,17 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic_per_update():
-    """DRAM bytes per gap site-update of the sampling colour pass from the committed
-    record of an ncu capture, or None when the kernel sources changed since."""
+def recorded_traffic_per_update(key="dram_bytes_per_gap_update"):
+    """A per-update figure of the sampling colour pass (DRAM bytes by default, or
+    issued thread-instructions) from the committed record of an ncu capture, or
+    None when the kernel sources changed since or the record lacks it."""
     if not os.path.exists(TRAFFIC_RECORD):
         return None
     with open(TRAFFIC_RECORD) as f:
         rec = json.load(f)
-    if rec.get("kernel_sources_sha16") != kernel_sources_hash():
+    if rec.get("kernel_sources_sha16") != kernel_sources_hash() or key not in rec:
         return None
-    return float(rec["dram_bytes_per_gap_update"])
+    return float(rec[key])
 
 
 def record_traffic(csv_path, size, command):
@@ -93,13 +94,33 @@ def record_traffic(csv_path, size, command):
         tot += float(hit[0][i].replace(",", "")) * scale[units[i]]
     w = synthetic.workload("lognormal4096", L=size)
     updates = int(w.gap[0].sum()) * w.chains / 2.0
-    rec = {"dram_bytes_per_gap_update": round(tot / updates, 4),
+    extra = {}
+    if "smsp__inst_executed.sum" in head:
+        inst = float(hit[0][head.index("smsp__inst_executed.sum")].replace(",", ""))
+        extra["thread_instructions_per_gap_update"] = round(inst * 32 / updates, 2)
+    rec = {"dram_bytes_per_gap_update": round(tot / updates, 4), **extra,
            "kernel": hit[0][k], "field_side": size, "updates_per_launch": updates,
            "dram_bytes_per_launch": tot, "kernel_sources_sha16": kernel_sources_hash(),
            "command": command}
     with open(TRAFFIC_RECORD, "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))
+
+
+def issue_ceiling(updates_per_s, clocks, dev):
+    """Issued thread-instructions/s of the sampling pass (recorded instructions per
+    update x its measured update rate) against the GPU's issue rate, or None
+    without a current record."""
+    import torch
+    ipu = recorded_traffic_per_update("thread_instructions_per_gap_update")
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if ipu is None or not mhz:
+        return None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 4 * 32 * mhz * 1e6
+    ach = ipu * updates_per_s
+    return {"achieved": ach, "peak": peak, "unit": "thread-instructions/s", "frac": ach / peak,
+            "thread_instructions_per_gap_update": ipu, "sms": sms, "sm_mhz": mhz}
 
 
 def max_over_ranks(values, device):
@@ -398,6 +419,9 @@ def run_gpu(args):
                      "kernel": "tiled_pass_kernel" if args.path == "tiled" else "plain_pass_kernel",
                      "alg_bytes_per_gap_update": alg_bytes_per_update,
                      "avg_launch_ms": launch_ms, "peak_kind": peak_kind},
+        # the ceiling the pass actually meets: instruction issue (SMs x 4 schedulers x
+        # 32 lanes x the sampled SM clock), with the recorded instructions per update
+        "issue": issue_ceiling(P * R / 2.0 / (launch_ms / 1e3), clocks, dev),
         # gap site-updates/s of the sweeps alone, by phase (equilibration: the run of
         # sweeps as one graph replay; measurement: the 100 sweeps as one replay)
         "phases": {"equil": P * R / (statistics.mean(equil_ms) / 1e3),
