@@ -77,3 +77,26 @@ def test_gpus_flag_starts_one_rank_per_device_and_reduces():
     assert len(lines) == 1, out.stdout
     assert lines[0]["n_gpus"] == 2 and lines[0]["ms"] == 110.0
     assert lines[0]["value"] == pytest.approx(1000 * 3 * 2 / 0.110)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores (the paper
+    ships no code) and prints one line with the reference keys."""
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=600, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["unit"] == "gap site-updates/s" and line["higher_is_better"] is True
