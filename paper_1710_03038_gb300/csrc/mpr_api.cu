@@ -213,9 +213,17 @@ struct mpr_ctx {
     // (n_f, n_fit, i_max)
     cudaGraphExec_t eq_exec = nullptr;
     long long eq_key = -1;
+    // tiled path: a second stream and two events, so that a colour pass's launch
+    // for its heavy tiles and the one for the chains left over by the chain
+    // groups run beside the main launch (they touch other tiles or chains)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~mpr_ctx() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
         if (eq_exec) cudaGraphExecDestroy(eq_exec);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         delete sub;
     }
 };
@@ -1039,6 +1047,14 @@ mpr_status init_impl(mpr_ctx* c, int n_img, const int* Lx, const int* Ly, int n_
                                  cudaMemcpyDeviceToHost, s));
         MPR_CUDA(cudaStreamSynchronize(s));
         MPR_TRY(split_tiles(c, tiles, s));
+        ChainRange cr[2];
+        const bool extra = c->n_light[0] < g.n_tiles || c->n_light[1] < g.n_tiles ||
+                           chain_ranges(c, cr) > 1;
+        if (extra && !c->side) {
+            MPR_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+            MPR_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+            MPR_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        }
     }
     long long maxn = 0;
     for (int i = 0; i < n_img; ++i) maxn = std::max(maxn, (long long)Lx[i] * Ly[i]);
@@ -1148,12 +1164,21 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
                 e = launch_plain_pass(a, c->g.max_Lx, c->g.max_Ly, s);
             } else {
                 const int nt = c->g.n_tiles, nl = c->n_light[colour];
+                // the heavy tiles and the remaining chains go to the side stream
+                // when there is a main launch for them to run beside
+                const bool extra = nl < nt || n_cr > 1;
+                const bool fork = extra && nl > 0 && c->side;
+                cudaStream_t s2 = fork ? c->side : s;
+                if (fork) {
+                    e = cudaEventRecord(c->ev_fork, s);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+                }
                 // whole chain groups: light tiles, then heavy ones
                 a.chain0 = cr[0].chain0;
                 a.chain_end = cr[0].chain_end;
                 a.chain_group = cr[0].group;
                 a.tile_list = nl < nt ? c->d_tile_list + (size_t)colour * nt : nullptr;
-                if (nl > 0) {  // the light tiles (all of them without a heavy launch)
+                if (e == cudaSuccess && nl > 0) {  // the light tiles (all of them without a heavy launch)
                     a.tile_base = 0;
                     a.n_list = nl;
                     a.gt = nl < nt ? c->gt_light[colour] : c->gt[colour];
@@ -1163,7 +1188,7 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
                     a.tile_base = nl;
                     a.n_list = nt - nl;
                     a.gt = c->gt[colour];
-                    e = launch_tiled_pass(a, c->g.tx, c->g.ty, s);
+                    e = launch_tiled_pass(a, c->g.tx, c->g.ty, s2);
                 }
                 if (e == cudaSuccess && n_cr > 1) {  // the remaining chains, every tile
                     a.chain0 = cr[1].chain0;
@@ -1173,7 +1198,11 @@ mpr_status launch_sweeps(mpr_ctx* c, int n, int phase, int flags, bool stats, bo
                     a.tile_base = 0;
                     a.n_list = nt;
                     a.gt = c->gt[colour];
-                    e = launch_tiled_pass(a, c->g.tx, c->g.ty, s);
+                    e = launch_tiled_pass(a, c->g.tx, c->g.ty, s2);
+                }
+                if (fork && e == cudaSuccess) {
+                    e = cudaEventRecord(c->ev_join, c->side);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
                 }
             }
             if (e != cudaSuccess) return fail(MPR_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
