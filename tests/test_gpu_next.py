@@ -49,12 +49,13 @@ def test_equilibrate_applies_the_slope_rule_and_matches_the_oracle():
     assert abs(hist[n - 1] - em[n_o - 1]) < 4e-3, (hist[n - 1], em[n_o - 1])
 
 
-@pytest.mark.parametrize("path", ["tiled", "plain"])
-def test_equilibrate_device_stop_equals_host_loop(path):
+@pytest.mark.parametrize("path,R,cg", [("tiled", 6, 0), ("plain", 6, 0), ("tiled", 36, 16)])
+def test_equilibrate_device_stop_equals_host_loop(path, R, cg):
     """On a side stream the equilibration runs as one graph whose while loop the stop
     rule ends on the device; on the legacy stream the host reads the rule's flag at
     every check.  Both stop after the same sweep with the same bits, for a stop by
-    the rule and for a stop at i_max."""
+    the rule and for a stop at i_max (with 36 chains in groups of 16 the passes
+    also fork their launch for the 4 chains left over to a second stream)."""
     zs, gs = [], []
     for k, (h, w) in enumerate([(64, 64), (40, 90)]):
         zs.append(synthetic.grf((h, w), nu=0.5, ell=6.0, mean=50, std=10, seed=900 + k).astype(np.float32))
@@ -63,7 +64,8 @@ def test_equilibrate_device_stop_equals_host_loop(path):
     for i_max in (300, 15):
         res = []
         for stream in (None, side):
-            ctx = mpr.Context(zs, gs, chains=6, params=mpr.Params(seed=SEED, path=path))
+            ctx = mpr.Context(zs, gs, chains=R,
+                              params=mpr.Params(seed=SEED, path=path, chain_group=cg))
             ctx.set_T([0.13, 0.2])
             n = ctx.equilibrate(n_f=5, n_fit=20, i_max=i_max, stream=stream)
             torch.cuda.synchronize()

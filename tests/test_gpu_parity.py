@@ -344,6 +344,36 @@ def test_heavy_tiles_launch_separately_and_agree_bitwise():
         assert np.allclose(a, b, rtol=1e-6, atol=1e-5)
 
 
+@pytest.mark.parametrize("R,cg", [(32, 32), (36, 16)])
+def test_side_stream_launches_in_graphs_equal_the_plain_path(R, cg):
+    """With heavy tiles (and, for 36 chains in groups of 16, a launch for the 4 chains
+    left over) a colour pass forks its extra launches to a second stream; replayed
+    from CUDA graphs on a non-default stream the states, accept counts and a equal
+    the plain path's bit for bit."""
+    zs, gs = ragged_images()
+    gs[0][16:32, 32:48] = 1  # one 16x16 tile entirely gap: a heavy launch
+    side = torch.cuda.Stream()
+    out = []
+    for path, kw in (("plain", {}), ("tiled", {"chain_group": cg})):
+        with torch.cuda.stream(side):
+            ctx = make_ctx(zs, gs, R, path, **kw)
+            ctx.set_T([0.2, 0.2, 0.1, 0.4], stream=side)
+            ctx.sweep(6, "equil", stream=side)   # graph replays (runs of 4 or more)
+            ctx.sweep(5, "measure", stream=side)
+            st = [t.clone() for t in ctx.get_state(stream=side)]
+            zh = [t.clone() for t in ctx.predict(stream=side)]
+        side.synchronize()
+        info = ctx.chain_info()
+        out.append(([t.cpu().numpy() for t in st], info, [t.cpu().numpy() for t in zh]))
+        ctx.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1]["a"], out[1][1]["a"])
+    assert np.array_equal(out[0][1]["accepted"], out[1][1]["accepted"])
+    for a, b in zip(out[0][2], out[1][2]):
+        assert np.allclose(a, b, rtol=1e-6, atol=1e-5)
+
+
 def test_determinism_same_state_same_result():
     """Colour-race canary: the same sweep from the same state gives identical bits."""
     zs, gs = ragged_images()
