@@ -322,3 +322,34 @@ def test_select_q_errors():
     with pytest.raises(mpr._lib.MprError) as err:
         mpr.select_q(z, g, hold, [0.6], chains=2, n_equil=2, n_meas=2)
     assert err.value.status == 1
+
+
+def test_select_q_from_host_buffers_equals_device_buffers():
+    """mpr_select_q stages host inputs itself: the same call with host pointers gives
+    the same scores and temperatures, bit for bit, as with device pointers."""
+    import ctypes as C
+    z, g, hold = _cv_inputs("grf64")
+    qs = [0.25, 0.5]
+    dev = mpr.select_q(z, g, hold, qs, chains=4, n_equil=20, n_meas=20,
+                       params=mpr.Params(seed=SEED), topts=mpr.TOpts(L=32, iters=3))
+    lib = mpr._lib.load()
+    pc, tc = mpr.Params(seed=SEED).c(), mpr.TOpts(L=32, iters=3).c()
+    nb = C.c_size_t()
+    mpr._lib.call("mpr_select_q_workspace_size", 64, 64, 4, C.byref(pc), C.byref(tc), C.byref(nb))
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    zh = np.ascontiguousarray(z, dtype=np.float32)
+    gh = np.ascontiguousarray(g, dtype=np.uint8)
+    hh = np.ascontiguousarray(hold, dtype=np.uint8)
+    qa = (C.c_double * 2)(*qs)
+    sc = (C.c_double * 2)()
+    Ts = (C.c_double * 2)()
+    qb = C.c_double()
+    st = lib.mpr_select_q(64, 64, zh.ctypes.data_as(C.c_void_p), gh.ctypes.data_as(C.c_void_p),
+                          hh.ctypes.data_as(C.c_void_p), mpr._lib.MPR_HOST, 2, qa, 4, 20, 20,
+                          C.byref(pc), C.byref(tc), C.c_void_p(ws.data_ptr()),
+                          C.c_size_t(ws.numel()), sc, Ts, C.byref(qb),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.mpr_last_error()
+    assert np.array_equal(np.array(sc[:]), dev["scores"])
+    assert np.array_equal(np.array(Ts[:]), dev["T"])
+    assert qb.value == dev["q"]
